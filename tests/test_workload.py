@@ -1,0 +1,35 @@
+"""The shared seeded input generator: shapes, determinism, subsets, model facts."""
+import numpy as np
+
+from paper_2606_05687_b300 import workload as W
+
+
+def test_shapes_and_dtypes():
+    b = W.generate(W.rl_scale_walking(B=5))
+    assert b.A.shape == (5, 20, 13, 13) and b.Bm.shape == (5, 20, 13, 24)
+    assert b.A.dtype == np.float32 and b.mask.dtype == np.uint32
+    s = W.generate(W.small_centroidal(B=3))
+    assert s.Bm.shape == (3, 10, 13, 12) and s.mu.shape == (3, 10, 2)
+
+
+def test_determinism_and_subsets():
+    spec = W.rl_scale_walking(B=16)
+    a = W.generate(spec)
+    b = W.generate(spec)
+    sub = W.generate(spec, instances=[3, 11])
+    for name in ("A", "Bm", "Q", "R", "ry", "xi0", "mu", "mask"):
+        assert np.array_equal(getattr(a, name), getattr(b, name))
+        assert np.array_equal(getattr(a, name)[[3, 11]], getattr(sub, name))
+
+
+def test_model_structure():
+    b = W.generate(W.rl_scale_walking(B=4))
+    # gravity state is constant: unit row in A, zero row in B
+    assert np.all(b.A[..., 12, :12] == 0) and np.all(b.A[..., 12, 12] == 1)
+    assert np.all(b.Bm[..., 12, :] == 0)
+    # linear-velocity rows of B are dt/m on each force component
+    assert np.allclose(b.Bm[..., 6, 0], 0.02 / W.MASS)
+    # walking gait: all points of one foot share a stance bit
+    st = b.stance()
+    assert np.array_equal(st[..., 0:4].min(-1), st[..., 0:4].max(-1))
+    assert 0.3 < st.mean() < 0.9
