@@ -1,0 +1,169 @@
+/*
+ * pinmpc.h -- C ABI of the batched parallel-in-horizon MPC-QP solver.
+ *
+ * Each instance b of a batch is the linear time-varying MPC problem of
+ * Sec. III (the standard form stated there, with C = I):
+ *
+ *   min  sum_{k=0}^{N-1} 1/2 ||xi_{k+1} - r^y_k||^2_{Q_k} + 1/2 ||u_k - r^u_k||^2_{R_k}
+ *   s.t. xi_{k+1} = A_k xi_k + B_k u_k + e_k,   xi_0 given,
+ *        u_k in U_k  (a product over contacts of contact sets).
+ *
+ * Contact sets (Sec. II-B names the friction pyramid and the contact wrench
+ * cone): a stance contact's components (t, n) lie in the generalized pyramid
+ * {|t_j| <= c_j n, 0 <= n <= n_max}; a swing contact's components are 0.
+ *   contact_dim 3 (point force f_x, f_y, f_z):   t = (f_x, f_y), c = (mu, mu)
+ *   contact_dim 6 (foot wrench f, tau):           t = (f_x, f_y, tau_x, tau_y, tau_z),
+ *       c = (mu, mu, d_y, d_x, mu*min(d_x, d_y)), d_x/d_y the foot half length/width.
+ *
+ * The solver is the velocity-form, variable-splitting ADMM of Sec. III
+ * (lifted state [xi_k; u_{k-1}], splits z = lifted state and v = Bbar du,
+ * closed-form horizon-parallel updates with per-stage caches J_k, H_k, and
+ * Nesterov acceleration with restart).  Every stage update of an iteration
+ * runs in parallel; there is no Riccati recursion in the iteration and no
+ * assembled QP.  To certify the tolerance the solver may additionally fix
+ * the active faces read off the iterate and solve that equality-constrained
+ * LQR exactly (a "polish", a backward Riccati scan), accepting it only when
+ * an on-device KKT certificate passes.
+ *
+ * Conventions
+ *   - All functions return an mpc_status; none aborts or traps.
+ *   - Floating-point data is FP32, row-major, instance-major: stage arrays are
+ *     [B][N][...] with the stage stride N = the view's N (<= N_max).
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*; NULL = the legacy default stream) and is asynchronous unless
+ *     stated otherwise.
+ *   - A handle is not thread-safe: use one handle per host thread/stream.
+ *   - Pointers may be device pointers or host pointers (pinned host memory
+ *     keeps the copies asynchronous); the library detects which.
+ */
+#ifndef PINMPC_H
+#define PINMPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mpc_status {
+    MPC_OK = 0,
+    MPC_ERR_INVALID_ARG = 1,  /* bad dimension, null required pointer, bad value */
+    MPC_ERR_OOM = 2,          /* workspace does not fit the memory budget / device */
+    MPC_ERR_CUDA = 3,         /* a CUDA call failed; see mpc_last_error */
+    MPC_ERR_STATE = 4,        /* call out of order (e.g. solve before set_stages) */
+    MPC_ERR_UNSUPPORTED = 5   /* valid request outside this build's limits */
+} mpc_status;
+
+/* Per-instance result codes written by mpc_get_traj's status array. */
+enum {
+    MPC_CONVERGED = 0,  /* KKT certificate <= kkt_tol */
+    MPC_MAX_ITER = 1,   /* iteration cap reached; outputs are the last iterate */
+    MPC_NONFINITE = 2,  /* NaN/Inf in this instance's inputs */
+    MPC_BAD_SET = 3,    /* empty contact set (n_max < 0 or mu < 0 on a stance contact) */
+    MPC_TIMEOUT = 4,    /* reserved for bounded device-side waits */
+    MPC_BAD_HORIZON = 5 /* horizon[b] outside [1, N] */
+};
+
+/* Solver configuration; fill with mpc_default_config then adjust. */
+typedef struct mpc_config {
+    int32_t nx;            /* state dimension (13 in this build) */
+    int32_t n_contacts;    /* contacts per stage: 8 (contact_dim 3) or 2 (contact_dim 6) */
+    int32_t contact_dim;   /* 3 or 6; nu = n_contacts * contact_dim */
+    int32_t B_max;         /* largest batch passed to mpc_set_stages */
+    int32_t N_max;         /* largest horizon (see mpc_max_horizon) */
+    float rho;             /* ADMM penalty (scaled form), > 0 (Sec. III's rho) */
+    float u_scale;         /* internal input scale sigma: the solver works in u/sigma */
+    int32_t max_iter;      /* ADMM iteration cap (the paper's experiments use 200) */
+    float kkt_tol;         /* certificate tolerance on the KKT residual */
+    int32_t check_start;   /* first iteration at which a certificate check runs */
+    int32_t check_every;   /* iterations between checks */
+    int32_t polish;        /* 1: polish on the read-off active set before certifying;
+                              0: certify the ADMM iterate itself (the plain method) */
+    int32_t accel;         /* 1: fast ADMM with restart; 0: plain ADMM */
+    float restart_eta;     /* restart threshold eta in (0, 1) */
+    float foot_half_length;/* d_x of the wrench cone (contact_dim 6) */
+    float foot_half_width; /* d_y of the wrench cone (contact_dim 6) */
+    uint64_t mem_budget;   /* device bytes this handle may allocate; 0 = no limit */
+    int32_t device;        /* CUDA device ordinal */
+} mpc_config;
+
+/* Stage data of one batch.  Arrays are instance-major with stage stride N. */
+typedef struct mpc_stage_view {
+    int32_t B;              /* instances in this batch, 1..B_max */
+    int32_t N;              /* stage stride of the arrays, 1..N_max */
+    const float* A;         /* [B][N][nx][nx]  required */
+    const float* Bm;        /* [B][N][nx][nu]  required */
+    const float* e;         /* [B][N][nx]      NULL = 0 */
+    const float* Q;         /* [B][N][nx]      diagonal of Q_k, > 0, required */
+    const float* R;         /* [B][N][nu]      diagonal of R_k, > 0, required */
+    const float* ry;        /* [B][N][nx]      state reference r^y_k, required */
+    const float* ru;        /* [B][N][nu]      input reference r^u_k, NULL = 0 */
+    const float* mu;        /* [B][N][nc]      friction coefficient per contact, required */
+    const float* fmax;      /* [B][N][nc]      normal-force bound per contact, required */
+    const uint32_t* mask;   /* [B][N]          bit c set = contact c in stance, required */
+    const float* xi0;       /* [B][nx]         initial state, required */
+    const float* u_prev;    /* [B][nu]         u_{-1} of the velocity form, NULL = 0 */
+    const int32_t* horizon; /* [B]            per-instance horizon <= N, NULL = N */
+} mpc_stage_view;
+
+typedef struct mpc_handle mpc_handle;
+
+/* Fill *cfg with defaults for the given problem shape (rho 100, u_scale
+ * 300, max_iter 1000, kkt_tol 1e-5, checks from iteration 20 every 10,
+ * polish on, acceleration on with eta 0.999, foot 0.10 x 0.05 m). */
+mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,
+                              int32_t contact_dim, int32_t B_max, int32_t N_max);
+
+/* Largest horizon this build supports for (nx, nu); 0 if the shape is not built. */
+int32_t mpc_max_horizon(int32_t nx, int32_t nu);
+
+/* Validate cfg, select its device and allocate the workspace (owned by the
+ * handle).  MPC_ERR_OOM if the workspace exceeds mem_budget or the device's
+ * free memory; MPC_ERR_UNSUPPORTED outside the build's limits. */
+mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out);
+
+/* Copy and repack the batch's stage data into the workspace on `stream`
+ * (Sec. III's stage matrices, scaled internally by u_scale).  The caller may
+ * reuse its buffers once `stream` has passed this call. */
+mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream);
+
+/* Solve instances [0, B) of the last set_stages batch on `stream`
+ * (asynchronous).  Convergence is reported per instance, not here. */
+mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream);
+
+/* Copy results of the last solve to caller buffers (device or host; any
+ * pointer may be NULL to skip it):
+ *   xi          [B][N][nx]  states xi_1..xi_N (xi_0 excluded)
+ *   u           [B][N][nu]  inputs u_0..u_{N-1}
+ *   status      [B]         MPC_CONVERGED / MPC_MAX_ITER / ...
+ *   iters       [B]         ADMM iterations run
+ *   kkt         [B]         KKT certificate of the returned (xi, u)
+ *   active_bits [B][N]      bit (c*F + f) = face f of contact c active, with
+ *                           F = 2*(contact_dim==3 ? 2 : 5) + 2 faces per contact
+ *                           ordered (+t_1, -t_1, +t_2, -t_2, ..., -n <= 0, n <= n_max);
+ *                           a face is active when g_f(u) >= -1e-5 (1 + n_max)
+ * Stages at or beyond an instance's horizon are written as 0.  With host
+ * pointers this call synchronizes `stream`. */
+mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status,
+                        int32_t* iters, float* kkt, uint64_t* active_bits, void* stream);
+
+/* Per-instance solver statistics of the last solve: polishes [B] = number
+ * of active-set polish attempts (Riccati scans) the instance ran.  Device
+ * or host pointer; host pointers synchronize `stream`. */
+mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream);
+
+/* Free the handle and its workspace (synchronizes the device first). */
+void mpc_destroy(mpc_handle* h);
+
+/* Last error message of h (or of the last failed mpc_create when h is NULL). */
+const char* mpc_last_error(mpc_handle* h);
+
+/* Bytes of device memory the handle owns. */
+uint64_t mpc_workspace_bytes(mpc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PINMPC_H */

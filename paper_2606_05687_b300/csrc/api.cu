@@ -1,0 +1,391 @@
+// Host side of the C ABI declared in include/pinmpc.h.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/pinmpc.h"
+#include "solve.cuh"
+
+using namespace pinmpc;
+
+namespace {
+
+// Shapes this build is compiled for: (nx, nu, contact_dim).
+using D24 = Dims<13, 24, 3>;  // 8 point contacts (4 corners per foot)
+using D12 = Dims<13, 12, 6>;  // 2 foot wrenches
+
+thread_local std::string g_create_error;
+
+struct Shape {
+    int srec, tail;
+    int (*smem_bytes)(int N);
+    cudaError_t (*set_smem_attr)(int bytes);
+    void (*launch_pack)(const PackArgs&, int B, cudaStream_t);
+    void (*launch_solve)(const SolveArgs&, int B, int n_rec, int smem, cudaStream_t);
+};
+
+template <class D>
+int smem_bytes_t(int N) { return Smem<D>(N).bytes(); }
+template <class D>
+cudaError_t set_smem_attr_t(int bytes) {
+    return cudaFuncSetAttribute(solve_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <class D>
+void launch_pack_t(const PackArgs& a, int B, cudaStream_t s) { pack_kernel<D><<<B, 256, 0, s>>>(a); }
+template <class D>
+void launch_solve_t(const SolveArgs& a, int B, int n_rec, int smem, cudaStream_t s) {
+    solve_kernel<D><<<B, 32 * a.N, smem, s>>>(a, n_rec);
+}
+template <class D>
+Shape make_shape() {
+    return Shape{D::SREC, D::TAIL, smem_bytes_t<D>, set_smem_attr_t<D>, launch_pack_t<D>, launch_solve_t<D>};
+}
+
+bool pick_shape(int nx, int nc, int cd, Shape* out) {
+    if (nx == 13 && cd == 3 && nc == 8) { *out = make_shape<D24>(); return true; }
+    if (nx == 13 && cd == 6 && nc == 2) { *out = make_shape<D12>(); return true; }
+    return false;
+}
+
+constexpr int kSmemLimit = 227 * 1024;
+
+int max_optin_smem(int device) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+        cudaGetLastError();
+        v = kSmemLimit;
+    }
+    return v;
+}
+
+}  // namespace
+
+struct mpc_handle {
+    mpc_config cfg{};
+    Shape shape{};
+    int nu = 0, nc = 0;
+    int irec = 0;          // floats per instance record
+    float* rec = nullptr;  // [B_max][irec]
+    float* out_xi = nullptr;
+    float* out_u = nullptr;
+    int* out_status = nullptr;
+    int* out_iters = nullptr;
+    float* out_kkt = nullptr;
+    unsigned long long* out_bits = nullptr;
+    int* out_npol = nullptr;
+    float* staging = nullptr;  // device copies of host-memory inputs
+    size_t staging_floats = 0;
+    uint64_t bytes = 0;
+    int B_set = 0, N_set = 0;
+    bool have_stages = false, have_solution = false;
+    int B_solved = 0;
+    std::string err;
+};
+
+static mpc_status fail(mpc_handle* h, mpc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return st;
+}
+
+static mpc_status cuda_fail(mpc_handle* h, cudaError_t e, const char* what) {
+    return fail(h, MPC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool is_host_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+extern "C" {
+
+mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, int32_t contact_dim,
+                              int32_t B_max, int32_t N_max) {
+    if (!cfg) return MPC_ERR_INVALID_ARG;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->nx = nx;
+    cfg->n_contacts = n_contacts;
+    cfg->contact_dim = contact_dim;
+    cfg->B_max = B_max;
+    cfg->N_max = N_max;
+    cfg->rho = 100.0f;
+    cfg->u_scale = 300.0f;
+    cfg->max_iter = 1000;
+    cfg->kkt_tol = 1e-5f;
+    cfg->check_start = 20;
+    cfg->check_every = 10;
+    cfg->polish = 1;
+    cfg->accel = 1;
+    cfg->restart_eta = 0.999f;
+    cfg->foot_half_length = 0.10f;
+    cfg->foot_half_width = 0.05f;
+    cfg->mem_budget = 0;
+    cfg->device = 0;
+    return MPC_OK;
+}
+
+int32_t mpc_max_horizon(int32_t nx, int32_t nu) {
+    Shape sh;
+    const int cd = (nu == 24) ? 3 : 6;
+    if (nu % cd != 0 || !pick_shape(nx, nu / cd, cd, &sh)) return 0;
+    int best = 0;
+    for (int N = 1; N <= 32; ++N)
+        if (sh.smem_bytes(N) <= kSmemLimit) best = N;
+    return best;
+}
+
+mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
+    g_create_error.clear();
+    if (!cfg || !out) return fail(nullptr, MPC_ERR_INVALID_ARG, "null config or output pointer");
+    *out = nullptr;
+    const mpc_config& c = *cfg;
+    Shape sh;
+    if (c.contact_dim != 3 && c.contact_dim != 6)
+        return fail(nullptr, MPC_ERR_INVALID_ARG, "contact_dim must be 3 or 6 (got %d)", c.contact_dim);
+    if (!pick_shape(c.nx, c.n_contacts, c.contact_dim, &sh))
+        return fail(nullptr, MPC_ERR_UNSUPPORTED,
+                    "shape nx=%d n_contacts=%d contact_dim=%d not built (built: 13/8/3, 13/2/6)", c.nx,
+                    c.n_contacts, c.contact_dim);
+    if (c.B_max < 1 || c.N_max < 1) return fail(nullptr, MPC_ERR_INVALID_ARG, "B_max and N_max must be >= 1");
+    if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||
+        c.check_every < 1 || c.check_start < 1 || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
+        !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f))
+        return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
+    if (c.N_max > 32)
+        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds 32 stages (one warp per stage)", c.N_max);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, MPC_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (c.device < 0 || c.device >= ndev) return fail(nullptr, MPC_ERR_INVALID_ARG, "bad device ordinal %d", c.device);
+    if ((e = cudaSetDevice(c.device)) != cudaSuccess) return fail(nullptr, MPC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    const int smem = sh.smem_bytes(c.N_max);
+    if (smem > max_optin_smem(c.device))
+        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d needs %d B shared memory per CTA (limit %d)", c.N_max,
+                    smem, max_optin_smem(c.device));
+    if ((e = sh.set_smem_attr(smem)) != cudaSuccess)
+        return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+
+    mpc_handle* h = new (std::nothrow) mpc_handle();
+    if (!h) return fail(nullptr, MPC_ERR_OOM, "host allocation failed");
+    h->cfg = c;
+    h->shape = sh;
+    h->nc = c.n_contacts;
+    h->nu = c.n_contacts * c.contact_dim;
+    h->irec = instance_record_floats(sh.srec, sh.tail, c.N_max);
+    const size_t B = (size_t)c.B_max, N = (size_t)c.N_max;
+    const size_t rec_b = B * h->irec * sizeof(float);
+    const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * h->nu * sizeof(float);
+    const size_t small_b = B * (3 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
+    h->bytes = rec_b + xi_b + u_b + small_b;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }
+    if ((c.mem_budget && h->bytes > c.mem_budget) || h->bytes > free_b) {
+        mpc_status st = fail(nullptr, MPC_ERR_OOM, "workspace %llu B exceeds budget %llu B / free %llu B",
+                             (unsigned long long)h->bytes, (unsigned long long)c.mem_budget,
+                             (unsigned long long)free_b);
+        delete h;
+        return st;
+    }
+    bool ok = cudaMalloc(&h->rec, rec_b) == cudaSuccess && cudaMalloc(&h->out_xi, xi_b) == cudaSuccess &&
+              cudaMalloc(&h->out_u, u_b) == cudaSuccess && cudaMalloc(&h->out_status, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->out_iters, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->out_kkt, B * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&h->out_bits, B * N * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&h->out_npol, B * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        const unsigned long long want = h->bytes;
+        mpc_destroy(h);
+        return fail(nullptr, MPC_ERR_OOM, "cudaMalloc of the %llu B workspace failed", want);
+    }
+    *out = h;
+    return MPC_OK;
+}
+
+mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!v) return fail(h, MPC_ERR_INVALID_ARG, "null stage view");
+    const mpc_config& c = h->cfg;
+    if (v->B < 1 || v->B > c.B_max) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, B_max=%d]", v->B, c.B_max);
+    if (v->N < 1 || v->N > c.N_max) return fail(h, MPC_ERR_INVALID_ARG, "N=%d outside [1, N_max=%d]", v->N, c.N_max);
+    if (!v->A || !v->Bm || !v->Q || !v->R || !v->ry || !v->mu || !v->fmax || !v->mask || !v->xi0)
+        return fail(h, MPC_ERR_INVALID_ARG, "a required stage array is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t B = v->B, N = v->N, nx = c.nx, nu = h->nu, nc = h->nc;
+    const void* src[13] = {v->A, v->Bm, v->e, v->Q, v->R, v->ry, v->ru, v->mu, v->fmax, v->xi0, v->u_prev, v->mask, v->horizon};
+    const size_t cnt[13] = {B * N * nx * nx, B * N * nx * nu, B * N * nx, B * N * nx, B * N * nu, B * N * nx,
+                            B * N * nu, B * N * nc, B * N * nc, B * nx, B * nu, B * N, B};
+    const void* dev[13];
+    bool any_host = false;
+    for (int i = 0; i < 13; ++i) any_host |= is_host_pointer(src[i]);
+    if (any_host) {
+        size_t need = 0;
+        for (int i = 0; i < 13; ++i) need += src[i] ? ((cnt[i] + 63) & ~size_t(63)) : 0;
+        if (need > h->staging_floats) {
+            if (h->staging) {
+                cudaFree(h->staging);
+                h->bytes -= h->staging_floats * 4;
+                h->staging = nullptr;
+                h->staging_floats = 0;
+            }
+            if (c.mem_budget && h->bytes + need * 4 > c.mem_budget)
+                return fail(h, MPC_ERR_OOM, "host-input staging of %llu B exceeds the memory budget",
+                            (unsigned long long)(need * 4));
+            if ((e = cudaMalloc(&h->staging, need * 4)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, MPC_ERR_OOM, "staging cudaMalloc failed");
+            }
+            h->staging_floats = need;
+            h->bytes += need * 4;
+        }
+        size_t off = 0;
+        for (int i = 0; i < 13; ++i) {
+            if (!src[i]) { dev[i] = nullptr; continue; }
+            if (is_host_pointer(src[i])) {
+                float* d = h->staging + off;
+                if ((e = cudaMemcpyAsync(d, src[i], cnt[i] * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                    return cuda_fail(h, e, "cudaMemcpyAsync (stage data)");
+                dev[i] = d;
+            } else {
+                dev[i] = src[i];
+            }
+            off += (cnt[i] + 63) & ~size_t(63);
+        }
+    } else {
+        for (int i = 0; i < 13; ++i) dev[i] = src[i];
+    }
+    PackArgs a{};
+    a.A = (const float*)dev[0]; a.Bm = (const float*)dev[1]; a.e = (const float*)dev[2];
+    a.Q = (const float*)dev[3]; a.R = (const float*)dev[4]; a.ry = (const float*)dev[5];
+    a.ru = (const float*)dev[6]; a.mu = (const float*)dev[7]; a.fmax = (const float*)dev[8];
+    a.xi0 = (const float*)dev[9]; a.u_prev = (const float*)dev[10];
+    a.mask = (const uint32_t*)dev[11]; a.horizon = (const int32_t*)dev[12];
+    a.N = (int)N;
+    a.n_rec = c.N_max;
+    a.irec = h->irec;
+    a.sigma = c.u_scale;
+    a.rec = h->rec;
+    h->shape.launch_pack(a, (int)B, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "pack kernel launch");
+    h->B_set = (int)B;
+    h->N_set = (int)N;
+    h->have_stages = true;
+    h->have_solution = false;
+    return MPC_OK;
+}
+
+mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_stages) return fail(h, MPC_ERR_STATE, "mpc_solve_batch before mpc_set_stages");
+    if (B < 1 || B > h->B_set) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_set);
+    const mpc_config& c = h->cfg;
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    SolveArgs a{};
+    a.rec = h->rec;
+    a.irec = h->irec;
+    a.N = h->N_set;
+    a.rho = c.rho;
+    a.sigma = c.u_scale;
+    a.kkt_tol = c.kkt_tol;
+    a.eta = c.restart_eta;
+    a.dx = c.foot_half_length;
+    a.dy = c.foot_half_width;
+    a.max_iter = c.max_iter;
+    a.check_start = c.check_start;
+    a.check_every = c.check_every;
+    a.polish = c.polish;
+    a.accel = c.accel;
+    a.out_xi = h->out_xi;
+    a.out_u = h->out_u;
+    a.out_status = h->out_status;
+    a.out_iters = h->out_iters;
+    a.out_kkt = h->out_kkt;
+    a.out_bits = h->out_bits;
+    a.out_npol = h->out_npol;
+    const int smem = h->shape.smem_bytes(h->N_set);
+    h->shape.launch_solve(a, B, c.N_max, smem, static_cast<cudaStream_t>(stream));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "solve kernel launch");
+    h->have_solution = true;
+    h->B_solved = B;
+    return MPC_OK;
+}
+
+mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status, int32_t* iters, float* kkt,
+                        uint64_t* active_bits, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_solution) return fail(h, MPC_ERR_STATE, "mpc_get_traj before mpc_solve_batch");
+    const mpc_config& c = h->cfg;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const size_t B = h->B_solved, N = h->N_set;
+    struct { void* dst; const void* src; size_t bytes; } cp[6] = {
+        {xi, h->out_xi, B * N * c.nx * 4}, {u, h->out_u, B * N * h->nu * 4}, {status, h->out_status, B * 4},
+        {iters, h->out_iters, B * 4}, {kkt, h->out_kkt, B * 4}, {active_bits, h->out_bits, B * N * 8}};
+    bool host = false;
+    for (auto& x : cp) {
+        if (!x.dst) continue;
+        host |= is_host_pointer(x.dst);
+        if ((e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDefault, s)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMemcpyAsync (results)");
+    }
+    if (host && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    return MPC_OK;
+}
+
+mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_solution) return fail(h, MPC_ERR_STATE, "mpc_get_stats before mpc_solve_batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (polishes) {
+        if ((e = cudaMemcpyAsync(polishes, h->out_npol, (size_t)h->B_solved * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMemcpyAsync (stats)");
+        if (is_host_pointer(polishes) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    return MPC_OK;
+}
+
+void mpc_destroy(mpc_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->cfg.device);
+    cudaDeviceSynchronize();
+    cudaFree(h->rec);
+    cudaFree(h->out_xi);
+    cudaFree(h->out_u);
+    cudaFree(h->out_status);
+    cudaFree(h->out_iters);
+    cudaFree(h->out_kkt);
+    cudaFree(h->out_bits);
+    cudaFree(h->out_npol);
+    cudaFree(h->staging);
+    cudaGetLastError();
+    delete h;
+}
+
+const char* mpc_last_error(mpc_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+uint64_t mpc_workspace_bytes(mpc_handle* h) { return h ? h->bytes : 0; }
+
+}  // extern "C"

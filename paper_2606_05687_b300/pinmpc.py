@@ -1,0 +1,220 @@
+"""Thin ctypes binding of the C ABI in include/pinmpc.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libpinmpc.so`` built from
+``csrc/``; this module only converts Python/torch arguments to the C structs
+and raw pointers.  A missing library raises ``ImportError`` (there is no
+Python or CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpinmpc.so")
+
+MPC_OK, MPC_ERR_INVALID_ARG, MPC_ERR_OOM, MPC_ERR_CUDA, MPC_ERR_STATE, MPC_ERR_UNSUPPORTED = range(6)
+CONVERGED, MAX_ITER, NONFINITE, BAD_SET, TIMEOUT, BAD_HORIZON = range(6)
+STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID_ARG", 2: "MPC_ERR_OOM", 3: "MPC_ERR_CUDA",
+                4: "MPC_ERR_STATE", 5: "MPC_ERR_UNSUPPORTED"}
+
+
+class MpcConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("n_contacts", ctypes.c_int32),
+                ("contact_dim", ctypes.c_int32), ("B_max", ctypes.c_int32),
+                ("N_max", ctypes.c_int32), ("rho", ctypes.c_float), ("u_scale", ctypes.c_float),
+                ("max_iter", ctypes.c_int32), ("kkt_tol", ctypes.c_float),
+                ("check_start", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("polish", ctypes.c_int32), ("accel", ctypes.c_int32),
+                ("restart_eta", ctypes.c_float), ("foot_half_length", ctypes.c_float),
+                ("foot_half_width", ctypes.c_float), ("mem_budget", ctypes.c_uint64),
+                ("device", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+
+
+class StageView(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("N", ctypes.c_int32), ("A", _P), ("Bm", _P), ("e", _P),
+                ("Q", _P), ("R", _P), ("ry", _P), ("ru", _P), ("mu", _P), ("fmax", _P),
+                ("mask", _P), ("xi0", _P), ("u_prev", _P), ("horizon", _P)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libpinmpc.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first")
+    lib = ctypes.CDLL(LIB_PATH)
+    lib.mpc_default_config.argtypes = [ctypes.POINTER(MpcConfig)] + [ctypes.c_int32] * 5
+    lib.mpc_default_config.restype = ctypes.c_int
+    lib.mpc_max_horizon.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.mpc_max_horizon.restype = ctypes.c_int32
+    lib.mpc_create.argtypes = [ctypes.POINTER(MpcConfig), ctypes.POINTER(ctypes.c_void_p)]
+    lib.mpc_create.restype = ctypes.c_int
+    lib.mpc_set_stages.argtypes = [ctypes.c_void_p, ctypes.POINTER(StageView), ctypes.c_void_p]
+    lib.mpc_set_stages.restype = ctypes.c_int
+    lib.mpc_solve_batch.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.mpc_solve_batch.restype = ctypes.c_int
+    lib.mpc_get_traj.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 6 + [ctypes.c_void_p]
+    lib.mpc_get_traj.restype = ctypes.c_int
+    lib.mpc_get_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mpc_get_stats.restype = ctypes.c_int
+    lib.mpc_destroy.argtypes = [ctypes.c_void_p]
+    lib.mpc_destroy.restype = None
+    lib.mpc_last_error.argtypes = [ctypes.c_void_p]
+    lib.mpc_last_error.restype = ctypes.c_char_p
+    lib.mpc_workspace_bytes.argtypes = [ctypes.c_void_p]
+    lib.mpc_workspace_bytes.restype = ctypes.c_uint64
+    _lib = lib
+    return lib
+
+
+class MpcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def default_config(nx: int, n_contacts: int, contact_dim: int, B_max: int, N_max: int,
+                   **overrides) -> MpcConfig:
+    lib = load()
+    cfg = MpcConfig()
+    st = lib.mpc_default_config(ctypes.byref(cfg), nx, n_contacts, contact_dim, B_max, N_max)
+    if st != MPC_OK:
+        raise MpcError(st, "mpc_default_config")
+    for k, v in overrides.items():
+        if not hasattr(cfg, k):
+            raise AttributeError(f"mpc_config has no field {k!r}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to the C ABI must be contiguous")
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):  # numpy
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the C ABI must be C-contiguous")
+        return t.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(t)}")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Solver:
+    """One ``mpc_handle``: create, set stages, solve, read results."""
+
+    def __init__(self, cfg: MpcConfig):
+        self.lib = load()
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = self.lib.mpc_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != MPC_OK:
+            raise MpcError(st, self.lib.mpc_last_error(None).decode())
+        self.h = h
+        self.nu = cfg.n_contacts * cfg.contact_dim
+
+    def _check(self, st: int, what: str):
+        if st != MPC_OK:
+            raise MpcError(st, f"{what}: {self.lib.mpc_last_error(self.h).decode()}")
+
+    def set_stages(self, B: int, N: int, *, A, Bm, Q, R, ry, mu, fmax, mask, xi0, e=None,
+                   ru=None, u_prev=None, horizon=None, stream=None):
+        v = StageView(B=B, N=N, A=_ptr(A), Bm=_ptr(Bm), e=_ptr(e), Q=_ptr(Q), R=_ptr(R),
+                      ry=_ptr(ry), ru=_ptr(ru), mu=_ptr(mu), fmax=_ptr(fmax), mask=_ptr(mask),
+                      xi0=_ptr(xi0), u_prev=_ptr(u_prev), horizon=_ptr(horizon))
+        self._keep = (A, Bm, Q, R, ry, mu, fmax, mask, xi0, e, ru, u_prev, horizon)
+        self._check(self.lib.mpc_set_stages(self.h, ctypes.byref(v), _stream_ptr(stream)),
+                    "mpc_set_stages")
+
+    def solve(self, B: int, stream=None):
+        self._check(self.lib.mpc_solve_batch(self.h, B, _stream_ptr(stream)), "mpc_solve_batch")
+
+    def get_traj(self, xi=None, u=None, status=None, iters=None, kkt=None, active_bits=None,
+                 stream=None):
+        self._check(self.lib.mpc_get_traj(self.h, _ptr(xi), _ptr(u), _ptr(status), _ptr(iters),
+                                          _ptr(kkt), _ptr(active_bits), _stream_ptr(stream)),
+                    "mpc_get_traj")
+
+    def get_stats(self, polishes=None, stream=None):
+        self._check(self.lib.mpc_get_stats(self.h, _ptr(polishes), _stream_ptr(stream)),
+                    "mpc_get_stats")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self.lib.mpc_workspace_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def device_inputs(batch, device="cuda", pin_host=False):
+    """The arrays of a ``workload.Batch`` as torch tensors on ``device`` (or in
+    pinned host memory with ``pin_host``), keyed by the stage-view names."""
+    import numpy as np
+    import torch
+    out = {}
+    for name in ("A", "Bm", "e", "Q", "R", "ry", "ru", "mu", "fmax", "xi0", "u_prev"):
+        out[name] = torch.from_numpy(np.ascontiguousarray(getattr(batch, name)))
+    out["mask"] = torch.from_numpy(np.ascontiguousarray(batch.mask).view(np.int32))
+    out["horizon"] = torch.from_numpy(np.ascontiguousarray(batch.horizon))
+    for k, t in out.items():
+        out[k] = t.pin_memory() if pin_host else t.to(device)
+    return out
+
+
+def solver_for(batch, **overrides) -> Solver:
+    """A Solver sized for ``batch`` (nx 13, its contact model), config overrides applied."""
+    cfg = default_config(batch.nx, batch.nc, batch.contact_dim, batch.B, batch.N, **overrides)
+    return Solver(cfg)
+
+
+def solve_workload(batch, solver: Optional[Solver] = None, device="cuda", **overrides):
+    """Solve every instance of ``batch`` on the GPU; returns numpy arrays
+    (xi [B,N,nx], u [B,N,nu], status, iters, kkt, active_bits, polishes)."""
+    import numpy as np
+    import torch
+    s = solver or solver_for(batch, **overrides)
+    t = device_inputs(batch, device)
+    B, N = batch.B, batch.N
+    s.set_stages(B, N, **t)
+    s.solve(B)
+    dev = torch.device(device)
+    xi = torch.empty((B, N, batch.nx), dtype=torch.float32, device=dev)
+    u = torch.empty((B, N, batch.nu), dtype=torch.float32, device=dev)
+    st = torch.empty(B, dtype=torch.int32, device=dev)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    kk = torch.empty(B, dtype=torch.float32, device=dev)
+    bits = torch.empty((B, N), dtype=torch.int64, device=dev)
+    npol = torch.empty(B, dtype=torch.int32, device=dev)
+    s.get_traj(xi, u, st, it, kk, bits)
+    s.get_stats(npol)
+    torch.cuda.synchronize(dev)
+    return dict(xi=xi.cpu().numpy(), u=u.cpu().numpy(), status=st.cpu().numpy(),
+                iters=it.cpu().numpy(), kkt=kk.cpu().numpy(),
+                active_bits=bits.cpu().numpy().view(np.uint64), polishes=npol.cpu().numpy())
