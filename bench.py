@@ -1,0 +1,357 @@
+"""Benchmark: batched centroidal MPC-QP solves per second on B300.
+
+One step = one pass of the whole hot path over one batch of the walking
+workload (B=4096 environments, horizon N=20, 8 point contacts, nu=24):
+mpc_set_stages (pack/scale) + mpc_solve_batch (caches, ADMM, polish,
+certificate, outputs) + mpc_get_traj, inputs resident in HBM.  Only solves
+whose KKT certificate is <= 1e-5 count.  `e2e` repeats the step through the
+same C ABI from pinned host buffers with the host<->device copies inside the
+timed region.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload.
+
+Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+         (N > 1 under torch.distributed.run: weak scaling, one batch per rank)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MPC QP solves/s at B=4096 N=20 (KKT≤1e-5); served p50/p99 solve latency"
+B_BENCH, N_BENCH, SEED = 4096, 20, 1002
+KKT_TOL = 1e-5
+# FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# dram bytes per solve-kernel launch from an ncu capture, keyed by the source hash it was taken on
+MEASURED_TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2606_05687_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def flops_per_solve(iters, polishes, N, nx=13, nu=24, nc=8):
+    """Algorithmic FP32 flops of one solve in the implemented (factored) form.
+
+    Per stage and ADMM iteration: 6 products with B (nx*nu), 3 with A (nx^2),
+    one each with S_k and W_k (nx^2) -- FMA = 2 flops -- plus ~15 vector
+    flops per lifted component and ~40 per contact projection.  Per polish
+    and stage: the Riccati step (S A, S Bt, Bt'S Bt, Bt'S A, Cholesky, nx+1
+    solves, S Bt K, A'G) and the rollout.  Setup: S_k, W_k formation and
+    inversion."""
+    nb = nx + nu
+    f_it = 2 * (6 * nx * nu + 5 * nx * nx) + 15 * nb + 40 * nc
+    f_ric = 2 * (nx * nx * nx + nx * nx * nu + nu * nu * nx + nu * nx * nx + nu ** 3 / 6
+                 + (nx + 1) * nu * nu + nx * nu * nx + nx * nx * nx) + 2 * (nx * nx + nx * nu)
+    f_setup = 2 * (nx * nx * nu + nx * nx * nb) + 2 * 2 * nx ** 3
+    return N * (iters * f_it + polishes * f_ric + f_setup)
+
+
+class Clocks:
+    """nvidia-smi clock sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [x for x in sm if smax and x >= 0.3 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------
+def _oracle_warm(_):
+    from oracle import qp  # noqa: F401
+    return 0
+
+
+def _oracle_chunk(spec, start, n):
+    from oracle import qp
+    from paper_2606_05687_b300 import workload as W
+    ids = [(start + i) % spec.B for i in range(n)]
+    batch = W.generate(spec, instances=ids)
+    for b in range(len(ids)):
+        qp.solve_instance(qp.instance(batch, b))
+    return len(ids)
+
+
+def oracle_sample(seconds: float, workers: int, start: int = 0):
+    """Time the FP64 oracle (as it stands) on instances start, start+1, ... of
+    the benchmark workload for about `seconds`; returns (solves, elapsed, workers)."""
+    import multiprocessing as mp
+    from concurrent.futures import FIRST_COMPLETED, ProcessPoolExecutor, wait
+    from paper_2606_05687_b300 import workload as W
+    spec = W.rl_scale_walking(B=B_BENCH, N=N_BENCH, seed=SEED)
+    chunk = 4
+    done = 0
+    nxt = start
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_warm, range(workers)))   # imports outside the timed window
+        t0 = time.perf_counter()
+        pend = set()
+        while len(pend) < 2 * workers:
+            pend.add(ex.submit(_oracle_chunk, spec, nxt % B_BENCH, chunk))
+            nxt += chunk
+        while pend:
+            fin, pend = wait(pend, return_when=FIRST_COMPLETED)
+            for f in fin:
+                done += f.result()
+            if time.perf_counter() - t0 < seconds:
+                while len(pend) < 2 * workers:
+                    pend.add(ex.submit(_oracle_chunk, spec, nxt % B_BENCH, chunk))
+                    nxt += chunk
+        elapsed = time.perf_counter() - t0
+    return done, elapsed, workers
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+WORKLOAD = "walking centroidal MPC, B=4096 N=20 nx=13 nu=24 (8 point contacts)"
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cores = host_cores()
+    per_step, total = [], 0
+    for s in range(args.warmup + args.steps):
+        n, el, _ = oracle_sample(args.ref_seconds, cores, start=64 * s)
+        if s >= args.warmup:
+            per_step.append(n / el)
+            total += n
+    v = statistics.mean(per_step)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B_BENCH / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": B_BENCH, "horizon": N_BENCH, "seed": SEED},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{total} instances over {args.steps} steps of ~{args.ref_seconds:.0f} s"
+                                       " (dense condensed-QP interior point + crossover, FP64)"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    # CPU baseline first: its spawned process pool starts before any GPU call (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, el, w = oracle_sample(args.cpu_seconds, host_cores())
+        cpu = {"value": n / el, "unit": "solves/s", "cores": w, "kind": "oracle",
+               "sample": f"{n} instances of the same workload in {el:.1f} s (FP64 oracle, one process per core)"}
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05687_b300 import pinmpc
+    from paper_2606_05687_b300 import workload as W
+
+    spec = W.rl_scale_walking(B=B_BENCH, N=N_BENCH, seed=SEED + 7919 * rank)
+    batch = W.generate(spec)
+    B, N = batch.B, batch.N
+    solver = pinmpc.solver_for(batch, max_iter=args.max_iter)
+    stream = torch.cuda.current_stream(dev)
+    t = pinmpc.device_inputs(batch, dev)
+    xi = torch.empty((B, N, 13), dtype=torch.float32, device=dev)
+    u = torch.empty((B, N, 24), dtype=torch.float32, device=dev)
+    st = torch.empty(B, dtype=torch.int32, device=dev)
+    it = torch.empty(B, dtype=torch.int32, device=dev)
+    kk = torch.empty(B, dtype=torch.float32, device=dev)
+    bits = torch.empty((B, N), dtype=torch.int64, device=dev)
+    npol = torch.empty(B, dtype=torch.int32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        solver.set_stages(B, N, **t, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        solver.solve(B, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        solver.get_traj(xi, u, st, it, kk, bits, stream=stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e_start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        e_end.record(stream)
+        barrier()
+    total_ms = e_start.elapsed_time(e_end)
+    solve_ms = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
+    pack_ms = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    solver.get_stats(npol, stream=stream)
+    torch.cuda.synchronize(dev)
+    polishes = npol.cpu().numpy()
+    status = st.cpu().numpy()
+    iters = it.cpu().numpy()
+    kkt = kk.cpu().numpy()
+    ok = int(((status == 0) & (kkt <= KKT_TOL)).sum())
+    value = world * ok / (ms_per_step / 1e3)
+
+    # end to end through the C ABI from pinned host buffers
+    h_in = pinmpc.device_inputs(batch, pin_host=True)
+    h_xi = torch.empty((B, N, 13), dtype=torch.float32).pin_memory()
+    h_u = torch.empty((B, N, 24), dtype=torch.float32).pin_memory()
+    h_st = torch.empty(B, dtype=torch.int32).pin_memory()
+    h_kk = torch.empty(B, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in (h_xi, h_u, h_st, h_kk))
+
+    def e2e_step():
+        solver.set_stages(B, N, **h_in, stream=stream)
+        solver.solve(B, stream=stream)
+        solver.get_traj(h_xi, h_u, h_st, None, h_kk, None, stream=stream)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_ok = int(((h_st.numpy() == 0) & (h_kk.numpy() <= KKT_TOL)).sum())
+    e2e_val = world * e2e_ok / e2e_s
+
+    if rank != 0:
+        return
+    flops = float(flops_per_solve(iters.astype(np.float64), polishes.astype(np.float64), N).sum())
+    solve_avg = statistics.mean(solve_ms)
+    achieved = flops / (solve_avg / 1e3) / 1e12
+    h = kernel_source_hash()
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": world * B, "horizon": N, "seed": SEED,
+                   "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
+                   "max_iter": args.max_iter},
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(h),
+                     "kernel": "solve_kernel", "kernel_ms": solve_avg, "pack_ms": statistics.mean(pack_ms),
+                     "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived)", "src": h},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "solve_stats": {"converged": ok, "iters_mean": float(iters.mean()),
+                        "iters_p99": float(np.percentile(iters, 99)), "iters_max": int(iters.max()),
+                        "kkt_max": float(kkt.max()), "polishes_mean": float(polishes.mean())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

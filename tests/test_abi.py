@@ -1,0 +1,90 @@
+"""The C-ABI library builds, loads, exports every declared symbol and matches
+the header's struct layout (CPU only: no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pinmpc.h")
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05687_b300 import pinmpc
+    return pinmpc
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpc_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(P):
+    lib = P.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}$", out, flags=re.M), n
+
+
+def test_struct_layout_matches_header(tmp_path, P):
+    src = tmp_path / "layout.c"
+    fields_cfg = [f[0] for f in P.MpcConfig._fields_]
+    fields_view = [f[0] for f in P.StageView._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pinmpc.h"', "int main(void){",
+             'printf("%zu\\n", sizeof(mpc_config));']
+    lines += [f'printf("%zu\\n", offsetof(mpc_config, {f}));' for f in fields_cfg]
+    lines += ['printf("%zu\\n", sizeof(mpc_stage_view));']
+    lines += [f'printf("%zu\\n", offsetof(mpc_stage_view, {f}));' for f in fields_view]
+    lines += ["return 0;}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(P.MpcConfig)] + [getattr(P.MpcConfig, f).offset for f in fields_cfg]
+    want += [ctypes.sizeof(P.StageView)] + [getattr(P.StageView, f).offset for f in fields_view]
+    assert got == want
+
+
+def test_defaults_and_limits(P):
+    cfg = P.default_config(13, 8, 3, 4096, 20)
+    assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(1e-5)
+    assert cfg.polish == 1 and cfg.accel == 1
+    lib = P.load()
+    assert lib.mpc_max_horizon(13, 24) >= 20
+    assert lib.mpc_max_horizon(13, 12) >= 20
+    assert lib.mpc_max_horizon(13, 7) == 0
+
+
+def test_argument_errors_without_device(P):
+    lib = P.load()
+    h = ctypes.c_void_p()
+    bad = P.default_config(13, 8, 4, 16, 20)
+    assert lib.mpc_create(ctypes.byref(bad), ctypes.byref(h)) == P.MPC_ERR_INVALID_ARG
+    assert b"contact_dim" in lib.mpc_last_error(None)
+    unsup = P.default_config(12, 8, 3, 16, 20)
+    assert lib.mpc_create(ctypes.byref(unsup), ctypes.byref(h)) == P.MPC_ERR_UNSUPPORTED
+    neg = P.default_config(13, 8, 3, 16, 20, rho=-1.0)
+    assert lib.mpc_create(ctypes.byref(neg), ctypes.byref(h)) == P.MPC_ERR_INVALID_ARG
+    assert lib.mpc_set_stages(None, None, None) == P.MPC_ERR_INVALID_ARG
+    assert lib.mpc_solve_batch(None, 1, None) == P.MPC_ERR_INVALID_ARG
+    assert lib.mpc_get_stats(None, None, None) == P.MPC_ERR_INVALID_ARG
+    lib.mpc_destroy(None)
+
+
+def test_no_device_is_an_error_not_a_fallback(P):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(P.MpcError) as ei:
+        P.Solver(P.default_config(13, 8, 3, 16, 20))
+    assert ei.value.code == P.MPC_ERR_CUDA
