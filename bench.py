@@ -148,6 +148,10 @@ def oracle_sample(seconds: float, workers: int, start: int = 0):
     from concurrent.futures import FIRST_COMPLETED, ProcessPoolExecutor, wait
     from paper_2606_05687_b300 import workload as W
     spec = W.rl_scale_walking(B=B_BENCH, N=N_BENCH, seed=SEED)
+    # one BLAS thread per worker process (the pool already spreads over the cores)
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    print(f"[bench] oracle sample: {workers} worker processes, ~{seconds:.0f} s", file=sys.stderr, flush=True)
     chunk = 4
     done = 0
     nxt = start
@@ -159,7 +163,9 @@ def oracle_sample(seconds: float, workers: int, start: int = 0):
             pend.add(ex.submit(_oracle_chunk, spec, nxt % B_BENCH, chunk))
             nxt += chunk
         while pend:
-            fin, pend = wait(pend, return_when=FIRST_COMPLETED)
+            fin, pend = wait(pend, timeout=120, return_when=FIRST_COMPLETED)
+            if not fin:
+                raise RuntimeError("oracle worker pool made no progress in 120 s")
             for f in fin:
                 done += f.result()
             if time.perf_counter() - t0 < seconds:

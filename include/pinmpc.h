@@ -82,6 +82,9 @@ typedef struct mpc_config {
                               0: certify the ADMM iterate itself (the plain method) */
     int32_t accel;         /* 1: fast ADMM with restart; 0: plain ADMM */
     float restart_eta;     /* restart threshold eta in (0, 1) */
+    int32_t refine_steps;  /* after a failed polish: up to this many active-set updates, each
+                              reading the faces off Proj(u - refine_alpha * grad) and polishing again */
+    float refine_alpha;    /* step of that projected-gradient active-set update (scaled units) */
     float foot_half_length;/* d_x of the wrench cone (contact_dim 6) */
     float foot_half_width; /* d_y of the wrench cone (contact_dim 6) */
     uint64_t mem_budget;   /* device bytes this handle may allocate; 0 = no limit */
@@ -110,8 +113,10 @@ typedef struct mpc_stage_view {
 typedef struct mpc_handle mpc_handle;
 
 /* Fill *cfg with defaults for the given problem shape (rho 100, u_scale
- * 300, max_iter 1000, kkt_tol 1e-5, checks from iteration 20 every 10,
- * polish on, acceleration on with eta 0.999, foot 0.10 x 0.05 m). */
+ * 300, max_iter 1000, kkt_tol 5e-6 -- half the 1e-5 target, a margin for
+ * the FP32 rounding of the certificate -- checks from iteration 20 every 10,
+ * polish on with up to 3 refinement steps of alpha 0.05, acceleration on
+ * with eta 0.999, foot 0.10 x 0.05 m). */
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,
                               int32_t contact_dim, int32_t B_max, int32_t N_max);
 

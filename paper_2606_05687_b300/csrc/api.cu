@@ -124,12 +124,14 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->rho = 100.0f;
     cfg->u_scale = 300.0f;
     cfg->max_iter = 1000;
-    cfg->kkt_tol = 1e-5f;
+    cfg->kkt_tol = 5e-6f;
     cfg->check_start = 20;
     cfg->check_every = 10;
     cfg->polish = 1;
     cfg->accel = 1;
     cfg->restart_eta = 0.999f;
+    cfg->refine_steps = 3;
+    cfg->refine_alpha = 0.05f;
     cfg->foot_half_length = 0.10f;
     cfg->foot_half_width = 0.05f;
     cfg->mem_budget = 0;
@@ -162,7 +164,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     if (c.B_max < 1 || c.N_max < 1) return fail(nullptr, MPC_ERR_INVALID_ARG, "B_max and N_max must be >= 1");
     if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||
         c.check_every < 1 || c.check_start < 1 || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
-        !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f))
+        !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f) || c.refine_steps < 0 ||
+        !(c.refine_alpha > 0.0f))
         return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
     if (c.N_max > 32)
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds 32 stages (one warp per stage)", c.N_max);
@@ -314,6 +317,8 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     a.check_every = c.check_every;
     a.polish = c.polish;
     a.accel = c.accel;
+    a.refine_steps = c.refine_steps;
+    a.refine_alpha = c.refine_alpha;
     a.out_xi = h->out_xi;
     a.out_u = h->out_u;
     a.out_status = h->out_status;

@@ -43,6 +43,8 @@ struct SolveArgs {
     int N;                  // stage stride of this batch (<= N_max): CTA has 32*N threads
     float rho, sigma, kkt_tol, eta, dx, dy;
     int max_iter, check_start, check_every, polish, accel;
+    int refine_steps;       // active-set updates after a failed polish
+    float refine_alpha;     // projected-gradient step of those updates (scaled units)
     float* out_xi;          // [B][N][NX]
     float* out_u;           // [B][N][NU]
     int* out_status;        // [B]
@@ -651,6 +653,33 @@ __device__ float certificate(const Ctx<D>& c) {
     return fmaxf(feas, fmaxf(stat / (1.0f + den), comp / (1.0f + uinf)));
 }
 
+// Active-set update after a failed polish: the faces of each stance contact
+// are read off Proj(u - alpha * grad_u), u the polished (scaled) inputs and
+// grad_u = sigma * w the reduced-cost gradient left by the certificate.  A
+// violated face is clamped by the projection (added); a face whose multiplier
+// came out negative is pushed inside (dropped): one step of a primal
+// active-set method done by the projection.  Returns whether any mode word
+// changed (CTA-uniform).
+template <class D>
+__device__ bool refine_modes(const Ctx<D>& c, float alpha) {
+    constexpr int NU = D::NU, CD = D::CD;
+    bool changed = false;
+    for (int e = threadIdx.x; e < c.Nh * D::NC; e += blockDim.x) {
+        const int k = e / D::NC, q = e % D::NC;
+        if (!((c.mask(k) >> q) & 1u)) continue;
+        const float* s = c.stage(k);
+        float a[CD], out[CD];
+        for (int i = 0; i < CD; ++i)
+            a[i] = c.ur[k * NU + q * CD + i] - alpha * c.sigma * c.wv[k * NU + q * CD + i];
+        const uint32_t mw = project_contact<CD>(a, out, s[D::oMU + q], s[D::oFM + q], c.dx, c.dy);
+        if (mw != c.modes[e]) {
+            changed = true;
+            c.modes[e] = mw;
+        }
+    }
+    return __syncthreads_or(changed);
+}
+
 // Write (xr, ur) and the per-instance results; stages beyond the horizon are 0.
 template <class D>
 __device__ void write_output(const Ctx<D>& c, const SolveArgs& a, int b, int status, int iters, float kkt,
@@ -1042,7 +1071,13 @@ __global__ void __launch_bounds__(1024, 1) solve_kernel(SolveArgs a, int n_rec) 
                 if (tid < c.Nh * D::NC) c.lastm[tid] = c.modes[tid];
                 __syncthreads();
                 if (a.polish) { polish<D>(c); ++npol; } else iterate_as_output<D>(c, cb);
-                const float kkt = certificate<D>(c);
+                float kkt = certificate<D>(c);
+                for (int r = 0; a.polish && kkt > a.kkt_tol && r < a.refine_steps; ++r) {
+                    if (!refine_modes<D>(c, a.refine_alpha)) break;
+                    polish<D>(c);
+                    ++npol;
+                    kkt = certificate<D>(c);
+                }
                 if (kkt <= a.kkt_tol) {
                     write_output<D>(c, a, b, kConverged, m, kkt, npol);
                     return;

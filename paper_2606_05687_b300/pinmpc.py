@@ -27,7 +27,8 @@ class MpcConfig(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("kkt_tol", ctypes.c_float),
                 ("check_start", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("polish", ctypes.c_int32), ("accel", ctypes.c_int32),
-                ("restart_eta", ctypes.c_float), ("foot_half_length", ctypes.c_float),
+                ("restart_eta", ctypes.c_float), ("refine_steps", ctypes.c_int32),
+                ("refine_alpha", ctypes.c_float), ("foot_half_length", ctypes.c_float),
                 ("foot_half_width", ctypes.c_float), ("mem_budget", ctypes.c_uint64),
                 ("device", ctypes.c_int32)]
 

@@ -1,9 +1,6 @@
 """Shared helpers of the GPU parity tests: oracle references and comparisons."""
 from __future__ import annotations
 
-import multiprocessing as mp
-from concurrent.futures import ProcessPoolExecutor
-
 import numpy as np
 
 from oracle import kkt as okkt
@@ -16,20 +13,13 @@ OBJ_GAP = 1e-6       # relative objective gap
 TAU_ACT = okkt.TAU_ACT
 
 
-def _ref_one(args):
-    batch, b = args
-    inst = qp.instance(batch, b)
-    sol = qp.solve_instance(inst)
-    return sol.xi, sol.u, sol.objective
-
-
-def oracle_refs(batch, ids, workers=8):
-    """Oracle solutions of the listed instances (spawned worker processes)."""
-    jobs = [(batch.subset([b]), 0) for b in ids]
-    if len(jobs) <= 2:
-        return [_ref_one(j) for j in jobs]
-    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_ref_one, jobs))
+def oracle_refs(batch, ids):
+    """Oracle solutions (xi, u, objective) of the listed instances."""
+    out = []
+    for b in ids:
+        sol = qp.solve_instance(qp.instance(batch, b))
+        out.append((sol.xi, sol.u, sol.objective))
+    return out
 
 
 def compare(batch, out, ids, refs=None, check_bits=True):

@@ -45,10 +45,14 @@ def test_rl_scale_full_size_launch(pinmpc):
     against the oracle, and properties that hold for every instance."""
     batch = W.generate(W.rl_scale_walking(B=4096, N=20, seed=1002))
     out = pinmpc.solve_workload(batch)
-    assert np.all(out["status"] == 0), np.unique(out["status"], return_counts=True)
-    assert out["kkt"].max() <= KKT_TOL
-    assert dynamics_residual(batch, out) <= 1e-6
+    dyn = dynamics_residual(batch, out)
     viol, swing = cone_violation(batch, out)
+    print("full size: status", np.unique(out["status"], return_counts=True), "kkt max", out["kkt"].max(),
+          "iters mean", out["iters"].mean(), "max", out["iters"].max(), "polishes mean", out["polishes"].mean(),
+          "dyn", dyn, "cone", viol, "swing", swing)
+    assert np.all(out["status"] == 0), np.flatnonzero(out["status"])[:20]
+    assert out["kkt"].max() <= KKT_TOL
+    assert dyn <= 1e-6
     assert viol <= 1e-6 and swing == 0.0
     ids = [0, 1, 517, 1024, 2047, 2048, 3071, 4095]
     compare(batch, out, ids)
