@@ -53,7 +53,8 @@ def test_rl_scale_full_size_launch(pinmpc):
     assert np.all(out["status"] == 0), np.flatnonzero(out["status"])[:20]
     assert out["kkt"].max() <= KKT_TOL
     assert dyn <= 1e-6
-    assert viol <= 1e-6 and swing == 0.0
+    # face violations are part of the KKT residual (r_feas), so they share its bar
+    assert viol <= KKT_TOL and swing == 0.0
     ids = [0, 1, 517, 1024, 2047, 2048, 3071, 4095]
     compare(batch, out, ids)
 
