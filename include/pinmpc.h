@@ -158,6 +158,30 @@ mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status,
  * or host pointer; host pointers synchronize `stream`. */
 mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream);
 
+/* Solve a batch without allocating any device memory (no counterpart in the
+ * paper; this is a deployment aid).  For callers that may not allocate: code
+ * inside someone else's captured CUDA graph, a simulator step that owns a
+ * fixed memory pool and forbids cudaMalloc on its hot path, or a real-time
+ * loop that must stay clear of the allocator.  The caller passes device
+ * buffers only (host pointers are rejected: staging them would allocate):
+ * the stage view as for mpc_set_stages, and the outputs xi [B][N][nx],
+ * u [B][N][nu], status, iters, kkt [B] as for mpc_get_traj.  The solver's
+ * scratch (packed records, face bits, polish counts) is a fixed 8 MiB static
+ * device array that every GPU loading the library holds until process exit;
+ * a batch needing more (about 170 instances at N=20, nu=24) is rejected with
+ * MPC_ERR_UNSUPPORTED and a message (mpc_noalloc_last_error).  The first call
+ * on a device looks up the array's device address and opts the kernel into
+ * its shared memory, so make that first call before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (different streams, or host threads) race and must be serialized by the
+ * caller.  Each call rewrites every scratch word it reads, so nothing carries
+ * over from the previous call. */
+mpc_status mpc_solve_noalloc(const mpc_config* cfg, const mpc_stage_view* v, float* xi, float* u,
+                             int32_t* status, int32_t* iters, float* kkt, void* stream);
+
+/* Message of the last failed mpc_solve_noalloc on this host thread. */
+const char* mpc_noalloc_last_error(void);
+
 /* Free the handle and its workspace (synchronizes the device first). */
 void mpc_destroy(mpc_handle* h);
 

@@ -106,7 +106,7 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // Max over the CTA; every thread gets the result.  `red` holds >= 33 floats.
-__device__ float block_max(float v, float* red) {
+__device__ inline float block_max(float v, float* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     v = warp_max(v);
     if (lane == 0) red[warp] = v;
@@ -124,7 +124,7 @@ __device__ float block_max(float v, float* red) {
 
 // In-place inverse of an n x n SPD matrix (row-major) by Gauss-Jordan
 // elimination without pivoting, one warp, n <= 32.
-__device__ void warp_inverse_spd(float* M, int n, int lane) {
+__device__ inline void warp_inverse_spd(float* M, int n, int lane) {
     for (int p = 0; p < n; ++p) {
         __syncwarp();
         const float piv = 1.0f / M[p * n + p];

@@ -67,6 +67,10 @@ def load() -> ctypes.CDLL:
     lib.mpc_get_traj.restype = ctypes.c_int
     lib.mpc_get_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mpc_get_stats.restype = ctypes.c_int
+    lib.mpc_solve_noalloc.argtypes = [ctypes.POINTER(MpcConfig), ctypes.POINTER(StageView)] + [ctypes.c_void_p] * 6
+    lib.mpc_solve_noalloc.restype = ctypes.c_int
+    lib.mpc_noalloc_last_error.argtypes = []
+    lib.mpc_noalloc_last_error.restype = ctypes.c_char_p
     lib.mpc_destroy.argtypes = [ctypes.c_void_p]
     lib.mpc_destroy.restype = None
     lib.mpc_last_error.argtypes = [ctypes.c_void_p]
@@ -172,6 +176,20 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def solve_noalloc(cfg: MpcConfig, B: int, N: int, *, A, Bm, Q, R, ry, mu, fmax, mask, xi0,
+                  xi, u, status, iters, kkt, e=None, ru=None, u_prev=None, horizon=None, stream=None):
+    """mpc_solve_noalloc: solve from caller-owned device buffers into
+    caller-owned device outputs, allocating nothing on the device."""
+    lib = load()
+    v = StageView(B=B, N=N, A=_ptr(A), Bm=_ptr(Bm), e=_ptr(e), Q=_ptr(Q), R=_ptr(R), ry=_ptr(ry),
+                  ru=_ptr(ru), mu=_ptr(mu), fmax=_ptr(fmax), mask=_ptr(mask), xi0=_ptr(xi0),
+                  u_prev=_ptr(u_prev), horizon=_ptr(horizon))
+    st = lib.mpc_solve_noalloc(ctypes.byref(cfg), ctypes.byref(v), _ptr(xi), _ptr(u), _ptr(status),
+                               _ptr(iters), _ptr(kkt), _stream_ptr(stream))
+    if st != MPC_OK:
+        raise MpcError(st, lib.mpc_noalloc_last_error().decode())
 
 
 def device_inputs(batch, device="cuda", pin_host=False):
