@@ -3,12 +3,13 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
 
 #include "../../include/pinmpc.h"
-#include "solve.cuh"
+#include "polish.cuh"
 
 using namespace pinmpc;
 
@@ -26,6 +27,11 @@ struct Shape {
     cudaError_t (*set_smem_attr)(int bytes);
     void (*launch_pack)(const PackArgs&, int B, cudaStream_t);
     void (*launch_solve)(const SolveArgs&, int B, int n_rec, int smem, cudaStream_t);
+    int (*polish_smem)(int N);
+    int (*state_floats)(int N);
+    cudaError_t (*set_round_attrs)(int round_bytes, int polish_bytes);
+    void (*launch_round)(const RoundArgs&, int B, int smem, cudaStream_t);
+    void (*launch_polish)(const RoundArgs&, int B, int smem, cudaStream_t);
 };
 
 template <class D>
@@ -41,8 +47,28 @@ void launch_solve_t(const SolveArgs& a, int B, int n_rec, int smem, cudaStream_t
     solve_kernel<D><<<B, 32 * a.N, smem, s>>>(a, n_rec);
 }
 template <class D>
+int polish_smem_t(int N) { return kPolishWarps * WarpSmem<D>(N).total * 4; }
+template <class D>
+int state_floats_t(int N) { return RoundState<D>::floats(N); }
+template <class D>
+cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(round_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(polish_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
+}
+template <class D>
+void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
+    round_kernel<D><<<B, 32 * a.N, smem, s>>>(a);
+}
+template <class D>
+void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
+    polish_kernel<D><<<(B + kPolishWarps - 1) / kPolishWarps, 32 * kPolishWarps, smem, s>>>(a, B);
+}
+template <class D>
 Shape make_shape() {
-    return Shape{D::SREC, D::TAIL, smem_bytes_t<D>, set_smem_attr_t<D>, launch_pack_t<D>, launch_solve_t<D>};
+    return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
+                 launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
+                 set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -77,6 +103,14 @@ struct mpc_handle {
     float* out_kkt = nullptr;
     unsigned long long* out_bits = nullptr;
     int* out_npol = nullptr;
+    float* cache = nullptr;      // [B_max][N_max][2][nx*nx] S_j, W_j
+    float* state = nullptr;      // [B_max][state floats] ADMM iterate between rounds
+    uint32_t* modes = nullptr;   // [B_max][N_max][nc]
+    uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
+    int* done = nullptr;         // [B_max]
+    int* active = nullptr;       // running-instance counter
+    int* active_host = nullptr;  // pinned host copy of the counter
+    float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
     float* staging = nullptr;  // device copies of host-memory inputs
     size_t staging_floats = 0;
     uint64_t bytes = 0;
@@ -183,6 +217,11 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
                     smem, max_optin_smem(c.device));
     if ((e = sh.set_smem_attr(smem)) != cudaSuccess)
         return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    if (sh.polish_smem(c.N_max) > max_optin_smem(c.device))
+        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: polish needs %d B shared memory", c.N_max,
+                    sh.polish_smem(c.N_max));
+    if ((e = sh.set_round_attrs(smem, sh.polish_smem(c.N_max))) != cudaSuccess)
+        return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
 
     mpc_handle* h = new (std::nothrow) mpc_handle();
     if (!h) return fail(nullptr, MPC_ERR_OOM, "host allocation failed");
@@ -195,7 +234,12 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t rec_b = B * h->irec * sizeof(float);
     const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * h->nu * sizeof(float);
     const size_t small_b = B * (3 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
-    h->bytes = rec_b + xi_b + u_b + small_b;
+    const size_t cache_b = B * N * 2 * c.nx * c.nx * sizeof(float);
+    const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
+    const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
+    const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
+    const size_t round_b = cache_b + state_b + 2 * modes_b + B * sizeof(int) + sizeof(int) + kst_b;
+    h->bytes = rec_b + xi_b + u_b + small_b + round_b;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }
     if ((c.mem_budget && h->bytes > c.mem_budget) || h->bytes > free_b) {
@@ -210,7 +254,12 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->out_iters, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->out_kkt, B * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&h->out_bits, B * N * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc(&h->out_npol, B * sizeof(int)) == cudaSuccess;
+              cudaMalloc(&h->out_npol, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->cache, cache_b) == cudaSuccess && cudaMalloc(&h->state, state_b) == cudaSuccess &&
+              cudaMalloc(&h->modes, modes_b) == cudaSuccess && cudaMalloc(&h->lastm, modes_b) == cudaSuccess &&
+              cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->active, sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess &&
+              cudaMallocHost(&h->active_host, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         const unsigned long long want = h->bytes;
@@ -302,33 +351,40 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     const mpc_config& c = h->cfg;
     cudaError_t e = cudaSetDevice(c.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-    SolveArgs a{};
-    a.rec = h->rec;
-    a.irec = h->irec;
-    a.N = h->N_set;
-    a.rho = c.rho;
-    a.sigma = c.u_scale;
-    a.kkt_tol = c.kkt_tol;
-    a.eta = c.restart_eta;
-    a.dx = c.foot_half_length;
-    a.dy = c.foot_half_width;
-    a.max_iter = c.max_iter;
-    a.check_start = c.check_start;
-    a.check_every = c.check_every;
-    a.polish = c.polish;
-    a.accel = c.accel;
-    a.refine_steps = c.refine_steps;
-    a.refine_alpha = c.refine_alpha;
-    a.out_xi = h->out_xi;
-    a.out_u = h->out_u;
-    a.out_status = h->out_status;
-    a.out_iters = h->out_iters;
-    a.out_kkt = h->out_kkt;
-    a.out_bits = h->out_bits;
-    a.out_npol = h->out_npol;
-    const int smem = h->shape.smem_bytes(h->N_set);
-    h->shape.launch_solve(a, B, c.N_max, smem, static_cast<cudaStream_t>(stream));
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "solve kernel launch");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RoundArgs r{};
+    r.rec = h->rec; r.irec = h->irec; r.n_rec = c.N_max; r.N = h->N_set;
+    r.rho = c.rho; r.sigma = c.u_scale; r.kkt_tol = c.kkt_tol; r.eta = c.restart_eta;
+    r.dx = c.foot_half_length; r.dy = c.foot_half_width;
+    r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
+    r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
+    r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
+    r.done = h->done; r.active = h->active; r.Kst = h->Kst;
+    r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
+    r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol;
+    const int round_smem = h->shape.smem_bytes(h->N_set);
+    const int polish_smem = h->shape.polish_smem(h->N_set);
+    if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMemsetAsync");
+    // rounds of ADMM iterations, each followed by the polish/certify kernel;
+    // stop once no instance is running (host reads the counter each round)
+    int m0 = 0;
+    for (;;) {
+        const int m1 = (m0 == 0) ? std::min(c.check_start, c.max_iter) : std::min(m0 + c.check_every, c.max_iter);
+        r.m0 = m0;
+        r.m1 = m1;
+        h->shape.launch_round(r, B, round_smem, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "round kernel launch");
+        if ((e = cudaMemsetAsync(h->active, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+        h->shape.launch_polish(r, B, polish_smem, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "polish kernel launch");
+        if (m1 >= c.max_iter) break;
+        if ((e = cudaMemcpyAsync(h->active_host, h->active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMemcpyAsync (counter)");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        if (*h->active_host == 0) break;
+        m0 = m1;
+    }
     h->have_solution = true;
     h->B_solved = B;
     return MPC_OK;
@@ -384,6 +440,14 @@ void mpc_destroy(mpc_handle* h) {
     cudaFree(h->out_kkt);
     cudaFree(h->out_bits);
     cudaFree(h->out_npol);
+    cudaFree(h->cache);
+    cudaFree(h->state);
+    cudaFree(h->modes);
+    cudaFree(h->lastm);
+    cudaFree(h->done);
+    cudaFree(h->active);
+    cudaFree(h->Kst);
+    cudaFreeHost(h->active_host);
     cudaFree(h->staging);
     cudaGetLastError();
     delete h;
