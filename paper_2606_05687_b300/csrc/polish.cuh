@@ -52,11 +52,16 @@ struct RoundArgs {
 template <class D>
 struct WarpSmem {
     static constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
-    static constexpr int oP = 0, op = oP + NX * NX, oS = op + NX, osv = oS + NX * NX, oSA = osv + NX,
-                         oSB = oSA + NX * NX, oSe = oSB + NX * NU, oet = oSe + NX, oot = oet + NX,
-                         oG = oot + NU, og2 = oG + NX * NX, oL = og2 + NX, oK = oL + NU * NU,
-                         out = oK + NU * NK, oFixed = ((out + NU) + 3) & ~3;
-    int xr, ur, y, wv, modes, red, total;
+    // every region starts on a 16-byte boundary (float4 traffic goes to oK and the stage buffers)
+    static constexpr int al(int x) { return (x + 3) & ~3; }
+    static constexpr int oP = 0, op = al(oP + NX * NX), oS = al(op + NX), osv = al(oS + NX * NX),
+                         oSA = al(osv + NX), oSB = al(oSA + NX * NX), oSe = al(oSB + NX * NU), oet = al(oSe + NX),
+                         oot = al(oet + NX), oG = al(oot + NU), og2 = al(oG + NX * NX), oL = al(og2 + NX),
+                         oK = al(oL + NU * NU), out = al(oK + NU * NK), obuf0 = al(out + NU),
+                         obuf1 = al(obuf0 + D::SREC), oFixed = al(obuf1 + D::SREC);
+    static_assert(oK % 4 == 0 && obuf0 % 4 == 0 && obuf1 % 4 == 0 && oFixed % 4 == 0, "16-byte regions");
+    static_assert((NU * NK) % 4 == 0 && D::SREC % 4 == 0, "float4 transfers");
+    int xr, ur, y, wv, modes, cmu, cfm, cmask, total;
     __host__ __device__ explicit WarpSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
@@ -65,8 +70,36 @@ struct WarpSmem {
         y = take(N * NX);
         wv = take(N * NU);
         modes = take(N * D::NC);
-        red = take(4);
+        cmu = take(N * D::NC);
+        cfm = take(N * D::NC);
+        cmask = take(N);
         total = o;
+    }
+};
+
+// Register prefetch of FLOATS consecutive floats (multiple of 4, 16-byte
+// aligned) by one warp, stored to shared memory later: the next stage's data
+// is in flight while the current stage computes.
+template <int FLOATS, bool READONLY>
+struct Prefetch {
+    static constexpr int V4 = FLOATS / 4;
+    static constexpr int PER = (V4 + 31) / 32;
+    float4 r[PER];
+    __device__ __forceinline__ void load(const float* src, int lane) {
+        const float4* s = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int idx = lane + 32 * t;
+            if (idx < V4) r[t] = READONLY ? __ldg(s + idx) : s[idx];
+        }
+    }
+    __device__ __forceinline__ void store(float* dst, int lane) const {
+        float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int idx = lane + 32 * t;
+            if (idx < V4) d[idx] = r[t];
+        }
     }
 };
 
@@ -80,28 +113,30 @@ struct WCtx {
     int Nh, lane;
     float sigma, dx, dy;
     __device__ WCtx(int N) : L(N) {}
-    __device__ const float* stage(int k) const { return rec + (size_t)k * D::SREC; }
+    __device__ const float* grec(int k) const { return rec + (size_t)k * D::SREC; }
+    __device__ float* buf(int k) const { return sm + ((k & 1) ? WarpSmem<D>::obuf1 : WarpSmem<D>::obuf0); }
     __device__ float* xr() const { return sm + L.xr; }
     __device__ float* ur() const { return sm + L.ur; }
     __device__ float* y() const { return sm + L.y; }
     __device__ float* wv() const { return sm + L.wv; }
-    __device__ uint32_t mask(int k) const { return __float_as_uint(__ldg(stage(k) + D::oMASK)); }
+    __device__ float mu(int k, int q) const { return sm[L.cmu + k * D::NC + q]; }
+    __device__ float fms(int k, int q) const { return sm[L.cfm + k * D::NC + q]; }
+    __device__ uint32_t mask(int k) const { return __float_as_uint(sm[L.cmask + k]); }
 };
 
-// Column i of the reduced input map of stage k (lane i < NU):
+// Column i of the reduced input map of one stage (lane i < NU), from the
+// stage's record s in shared memory:
 // bt = Bs T e_i, rt = (T'RsT)_ii (1 for an eliminated column), gt = (T'Rs(o - rus))_i, ot = o_i.
 template <class D>
-__device__ __forceinline__ void reduced_column(const WCtx<D>& w, int k, int i, float* bt, float& rt, float& gt,
-                                               float& ot) {
+__device__ __forceinline__ void reduced_column(const WCtx<D>& w, const float* s, uint32_t mw, int i, float* bt,
+                                               float& rt, float& gt, float& ot) {
     constexpr int NX = D::NX, NU = D::NU, CD = D::CD;
-    const float* s = w.stage(k);
     const int q = i / CD, j = i % CD, base = q * CD;
-    const uint32_t mw = w.modes[k * D::NC + q];
     const bool swing = (mw & kSwingBit) != 0;
     const bool apex = (mw >> (2 * D::M)) & 1u;
     const bool top = (mw >> (2 * D::M + 1)) & 1u;
-    const float fms = __ldg(s + D::oFM + q);
-    const float mu = __ldg(s + D::oMU + q);
+    const float fms = s[D::oFM + q];
+    const float mu = s[D::oMU + q];
 #pragma unroll
     for (int r = 0; r < NX; ++r) bt[r] = 0.0f;
     rt = 1.0f;
@@ -110,20 +145,20 @@ __device__ __forceinline__ void reduced_column(const WCtx<D>& w, int k, int i, f
     if (swing || apex) return;
     if (j == D::NRM) {
         if (top) { ot = fms; return; }
-        rt = __ldg(s + D::oR + i);
-        gt = -rt * __ldg(s + D::oRU + i);
+        rt = s[D::oR + i];
+        gt = -rt * s[D::oRU + i];
 #pragma unroll
-        for (int r = 0; r < NX; ++r) bt[r] = __ldg(s + D::oB + r * NU + i);
+        for (int r = 0; r < NX; ++r) bt[r] = s[D::oB + r * NU + i];
         for (int jj = 0; jj < D::M; ++jj) {
             const int sg = face_sign(mw, jj);
             if (sg == 0) continue;
             const int tj = base + Cone<CD>::tang(jj);
             const float cj = sg * cone_coef<CD>(jj, mu, w.dx, w.dy);
-            const float rtj = __ldg(s + D::oR + tj);
+            const float rtj = s[D::oR + tj];
             rt += cj * cj * rtj;
-            gt -= cj * rtj * __ldg(s + D::oRU + tj);
+            gt -= cj * rtj * s[D::oRU + tj];
 #pragma unroll
-            for (int r = 0; r < NX; ++r) bt[r] = fmaf(cj, __ldg(s + D::oB + r * NU + tj), bt[r]);
+            for (int r = 0; r < NX; ++r) bt[r] = fmaf(cj, s[D::oB + r * NU + tj], bt[r]);
         }
         return;
     }
@@ -133,10 +168,27 @@ __device__ __forceinline__ void reduced_column(const WCtx<D>& w, int k, int i, f
         if (top) ot = sg * cone_coef<CD>(jj, mu, w.dx, w.dy) * fms;
         return;
     }
-    rt = __ldg(s + D::oR + i);
-    gt = -rt * __ldg(s + D::oRU + i);
+    rt = s[D::oR + i];
+    gt = -rt * s[D::oRU + i];
 #pragma unroll
-    for (int r = 0; r < NX; ++r) bt[r] = __ldg(s + D::oB + r * NU + i);
+    for (int r = 0; r < NX; ++r) bt[r] = s[D::oB + r * NU + i];
+}
+
+// x_{k+1} = A x_k + Bs u_k + e_k for lanes < NX (stage record s in shared memory)
+template <class D>
+__device__ __forceinline__ void rollout_step(const WCtx<D>& w, const float* s, int k) {
+    constexpr int NX = D::NX, NU = D::NU;
+    if (w.lane < NX) {
+        const float* xk = w.xr() + k * NX;
+        const float* u = w.ur() + k * NU;
+        float acc = s[D::oE + w.lane];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) acc = fmaf(s[D::oA + w.lane * NX + c], xk[c], acc);
+#pragma unroll
+        for (int i = 0; i < NU; ++i) acc = fmaf(s[D::oB + w.lane * NU + i], u[i], acc);
+        w.xr()[(k + 1) * NX + w.lane] = acc;
+    }
+    __syncwarp();
 }
 
 // Backward Riccati scan + forward rollout of one instance by one warp.
@@ -162,32 +214,38 @@ __device__ void warp_polish(const WCtx<D>& w) {
     for (int e = lane; e < NX * NX + NX; e += 32) {
         if (e < NX * NX) P[e] = 0.0f; else p[e - NX * NX] = 0.0f;
     }
-    __syncwarp();
+    Prefetch<D::SREC, true> pf;
+    pf.load(w.grec(w.Nh - 1), lane);
     for (int k = w.Nh - 1; k >= 0; --k) {
-        const float* s = w.stage(k);
+        float* s = w.buf(k);
+        pf.store(s, lane);
+        __syncwarp();
+        if (k > 0) pf.load(w.grec(k - 1), lane);
         float bt[NX], rt = 1.0f, gt = 0.0f, ot = 0.0f;
-        if (lane < NU) reduced_column<D>(w, k, lane, bt, rt, gt, ot);
-        else {
+        if (lane < NU) {
+            reduced_column<D>(w, s, w.modes[k * D::NC + lane / D::CD], lane, bt, rt, gt, ot);
+            ot_s[lane] = ot;
+        } else {
 #pragma unroll
             for (int r = 0; r < NX; ++r) bt[r] = 0.0f;
         }
-        if (lane < NU) ot_s[lane] = ot;
         __syncwarp();
         // et = e + Bs ot ; S = diag(Q) + P ; s = Q ry + p
         if (lane < NX) {
-            float acc = __ldg(s + D::oE + lane);
-            for (int i = 0; i < NU; ++i) acc = fmaf(__ldg(s + D::oB + lane * NU + i), ot_s[i], acc);
+            float acc = s[D::oE + lane];
+#pragma unroll
+            for (int i = 0; i < NU; ++i) acc = fmaf(s[D::oB + lane * NU + i], ot_s[i], acc);
             et[lane] = acc;
-            sv[lane] = fmaf(__ldg(s + D::oQ + lane), __ldg(s + D::oRY + lane), p[lane]);
+            sv[lane] = fmaf(s[D::oQ + lane], s[D::oRY + lane], p[lane]);
         }
         for (int e = lane; e < NX * NX; e += 32) {
             const int r = e / NX, c = e % NX;
-            S[e] = P[e] + (r == c ? __ldg(s + D::oQ + r) : 0.0f);
+            S[e] = P[e] + (r == c ? s[D::oQ + r] : 0.0f);
         }
         __syncwarp();
-        // SB column lane = S bt ; SA and Se
+        // SB column lane = S bt ; SA column / Se by lanes 0..NX
         if (lane < NU) {
-#pragma unroll
+#pragma unroll 1
             for (int r = 0; r < NX; ++r) {
                 float acc = 0.0f;
 #pragma unroll
@@ -195,97 +253,98 @@ __device__ void warp_polish(const WCtx<D>& w) {
                 SB[r * NU + lane] = acc;
             }
         }
-        for (int cidx = lane; cidx < NX + 1; cidx += 32) {
-            if (cidx < NX) {
-                float a[NX];
+        if (lane <= NX) {
+            float a[NX];
 #pragma unroll
-                for (int r = 0; r < NX; ++r) a[r] = __ldg(s + D::oA + r * NX + cidx);
+            for (int r = 0; r < NX; ++r) a[r] = (lane < NX) ? s[D::oA + r * NX + lane] : et[r];
+#pragma unroll 1
+            for (int r = 0; r < NX; ++r) {
+                float acc = 0.0f;
 #pragma unroll
-                for (int r = 0; r < NX; ++r) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < NX; ++c) acc = fmaf(S[r * NX + c], a[c], acc);
-                    SA[r * NX + cidx] = acc;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < NX; ++r) {
-                    float acc = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < NX; ++c) acc = fmaf(S[r * NX + c], et[c], acc);
-                    Se[r] = acc;
-                }
+                for (int c = 0; c < NX; ++c) acc = fmaf(S[r * NX + c], a[c], acc);
+                if (lane < NX) SA[r * NX + lane] = acc; else Se[r] = acc;
             }
         }
         __syncwarp();
-        // row lane of M = Rt + Bt' S Bt and of RHS = [-Bt' S A | Bt'(s - S et) - gt]
+        // row lane of M = Rt + Bt' S Bt (to shared memory, then registers) and of
+        // RHS = [-Bt' S A | Bt'(s - S et) - gt] (registers)
         float m[NU], x[NK];
+        if (lane < NU) {
+#pragma unroll 1
+            for (int j = 0; j < NU; ++j) {
+                float acc = (j == lane) ? rt : 0.0f;
 #pragma unroll
-        for (int j = 0; j < NU; ++j) {
-            float acc = (j == lane) ? rt : 0.0f;
+                for (int r = 0; r < NX; ++r) acc = fmaf(bt[r], SB[r * NU + j], acc);
+                Ls[lane * NU + j] = acc;
+            }
+#pragma unroll 1
+            for (int c = 0; c < NX; ++c) {
+                float acc = 0.0f;
 #pragma unroll
-            for (int r = 0; r < NX; ++r) acc = fmaf(bt[r], SB[r * NU + j], acc);
-            m[j] = acc;
-        }
-#pragma unroll
-        for (int c = 0; c < NX; ++c) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int r = 0; r < NX; ++r) acc = fmaf(bt[r], SA[r * NX + c], acc);
-            x[c] = -acc;
-        }
-        {
+                for (int r = 0; r < NX; ++r) acc = fmaf(bt[r], SA[r * NX + c], acc);
+                Ks[lane * NK + c] = -acc;
+            }
             float acc = -gt;
 #pragma unroll
             for (int r = 0; r < NX; ++r) acc = fmaf(bt[r], sv[r] - Se[r], acc);
-            x[NX] = acc;
+            Ks[lane * NK + NX] = acc;
         }
-        // Cholesky M = L L' in registers (lane = row)
+        __syncwarp();
 #pragma unroll
+        for (int j = 0; j < NU; ++j) m[j] = (lane < NU) ? Ls[lane * NU + j] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < NK; ++q) x[q] = (lane < NU) ? Ks[lane * NK + q] : 0.0f;
+        __syncwarp();
+        // Cholesky M = L L' (lane = row).  The row is kept shifted so that the
+        // current pivot column is m[0]: step p uses m[cc] = M[lane][p + cc], and
+        // column p of L is written to shared memory.
+#pragma unroll 1
         for (int pp = 0; pp < NU; ++pp) {
-            const float d = sqrtf(fmaxf(__shfl_sync(0xffffffffu, m[pp], pp), 1e-30f));
-            if (lane == pp) m[pp] = d;
-            else if (lane > pp) m[pp] = m[pp] / d;
-            const float lp = m[pp];
+            const float d = sqrtf(fmaxf(__shfl_sync(0xffffffffu, m[0], pp), 1e-30f));
+            const float l = (lane == pp) ? d : ((lane > pp) ? m[0] / d : 0.0f);
+            if (lane < NU) Ls[lane * NU + pp] = l;
 #pragma unroll
-            for (int c = pp + 1; c < NU; ++c) {
-                const float lcp = __shfl_sync(0xffffffffu, lp, c);
-                if (lane >= c) m[c] = fmaf(-lp, lcp, m[c]);
+            for (int cc = 1; cc < NU; ++cc) {
+                const int c = pp + cc;
+                const float lc = __shfl_sync(0xffffffffu, l, c & 31);
+                if (c < NU && lane >= c) m[cc] = fmaf(-l, lc, m[cc]);
             }
+#pragma unroll
+            for (int cc = 0; cc + 1 < NU; ++cc) m[cc] = m[cc + 1];
+            m[NU - 1] = 0.0f;
         }
+        __syncwarp();
         // forward substitution L y = RHS (rows in registers)
-#pragma unroll
+#pragma unroll 1
         for (int i = 0; i < NU; ++i) {
+            const float li = (lane < NU) ? Ls[lane * NU + i] : 0.0f;  // L[lane][i]
             if (lane == i) {
+                const float inv = 1.0f / li;
 #pragma unroll
-                for (int q = 0; q < NK; ++q) x[q] = x[q] / m[i];
+                for (int q = 0; q < NK; ++q) x[q] *= inv;
             }
 #pragma unroll
             for (int q = 0; q < NK; ++q) {
                 const float xi = __shfl_sync(0xffffffffu, x[q], i);
-                if (lane > i) x[q] = fmaf(-m[i], xi, x[q]);
+                if (lane > i) x[q] = fmaf(-li, xi, x[q]);
             }
         }
-        // L to shared memory for the transposed solve
-        if (lane < NU) {
-#pragma unroll
-            for (int c = 0; c < NU; ++c) Ls[lane * NU + c] = (c <= lane) ? m[c] : 0.0f;
-        }
-        __syncwarp();
         // backward substitution L' x = y
-#pragma unroll
+#pragma unroll 1
         for (int i = NU - 1; i >= 0; --i) {
             if (lane == i) {
+                const float inv = 1.0f / Ls[i * NU + i];
 #pragma unroll
-                for (int q = 0; q < NK; ++q) x[q] = x[q] / m[i];
+                for (int q = 0; q < NK; ++q) x[q] *= inv;
             }
-            const float lir = (lane < i) ? Ls[i * NU + lane] : 0.0f;
+            const float lir = (lane < i) ? Ls[i * NU + lane] : 0.0f;  // L[i][lane]
 #pragma unroll
             for (int q = 0; q < NK; ++q) {
                 const float xi = __shfl_sync(0xffffffffu, x[q], i);
                 if (lane < i) x[q] = fmaf(-lir, xi, x[q]);
             }
         }
+        __syncwarp();
         if (lane < NU) {
             float* Kg = w.K + (size_t)k * NU * NK + lane * NK;
 #pragma unroll
@@ -296,6 +355,7 @@ __device__ void warp_polish(const WCtx<D>& w) {
         }
         __syncwarp();
         // G = SA + SB K, g2 = s - Se - SB kappa
+#pragma unroll 1
         for (int e = lane; e < NX * NX + NX; e += 32) {
             if (e < NX * NX) {
                 const int r = e / NX, c = e % NX;
@@ -313,21 +373,22 @@ __device__ void warp_polish(const WCtx<D>& w) {
         }
         __syncwarp();
         // P = sym(A' G), p = A' g2
+#pragma unroll 1
         for (int e = lane; e < NX * NX + NX; e += 32) {
             if (e < NX * NX) {
                 const int r = e / NX, c = e % NX;
                 float a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
-                    a1 = fmaf(__ldg(s + D::oA + i * NX + r), G[i * NX + c], a1);
-                    a2 = fmaf(__ldg(s + D::oA + i * NX + c), G[i * NX + r], a2);
+                    a1 = fmaf(s[D::oA + i * NX + r], G[i * NX + c], a1);
+                    a2 = fmaf(s[D::oA + i * NX + c], G[i * NX + r], a2);
                 }
                 P[e] = 0.5f * (a1 + a2);
             } else {
                 const int r = e - NX * NX;
                 float acc = 0.0f;
 #pragma unroll
-                for (int i = 0; i < NX; ++i) acc = fmaf(__ldg(s + D::oA + i * NX + r), g2[i], acc);
+                for (int i = 0; i < NX; ++i) acc = fmaf(s[D::oA + i * NX + r], g2[i], acc);
                 p[r] = acc;
             }
         }
@@ -335,14 +396,23 @@ __device__ void warp_polish(const WCtx<D>& w) {
     }
     // forward rollout: ut = K x + kappa, u = T ut + o, x' = A x + Bs u + e
     float* ut = sm + WS::out;
+    Prefetch<D::NU * NK, false> pk;
+    pf.load(w.grec(0), lane);
+    pk.load(w.K, lane);
     for (int k = 0; k < w.Nh; ++k) {
-        const float* s = w.stage(k);
+        float* s = w.buf(k);
+        pf.store(s, lane);
+        pk.store(Ks, lane);
+        __syncwarp();
+        if (k + 1 < w.Nh) {
+            pf.load(w.grec(k + 1), lane);
+            pk.load(w.K + (size_t)(k + 1) * NU * NK, lane);
+        }
         const float* xk = w.xr() + k * NX;
         if (lane < NU) {
-            const float* Kg = w.K + (size_t)k * NU * NK + lane * NK;
-            float acc = Kg[NX];
+            float acc = Ks[lane * NK + NX];
 #pragma unroll
-            for (int r = 0; r < NX; ++r) acc = fmaf(Kg[r], xk[r], acc);
+            for (int r = 0; r < NX; ++r) acc = fmaf(Ks[lane * NK + r], xk[r], acc);
             ut[lane] = acc;
         }
         __syncwarp();
@@ -356,8 +426,8 @@ __device__ void warp_polish(const WCtx<D>& w) {
             if (swing || apex) {
                 for (int i = 0; i < D::CD; ++i) u[base + i] = 0.0f;
             } else {
-                const float mu = __ldg(s + D::oMU + q);
-                const float n = top ? __ldg(s + D::oFM + q) : ut[base + D::NRM];
+                const float mu = s[D::oMU + q];
+                const float n = top ? s[D::oFM + q] : ut[base + D::NRM];
                 u[base + D::NRM] = n;
                 for (int jj = 0; jj < D::M; ++jj) {
                     const int tj = base + Cone<D::CD>::tang(jj);
@@ -367,34 +437,21 @@ __device__ void warp_polish(const WCtx<D>& w) {
             }
         }
         __syncwarp();
-        if (lane < NX) {
-            const float* u = w.ur() + k * NU;
-            float acc = __ldg(s + D::oE + lane);
-#pragma unroll
-            for (int c = 0; c < NX; ++c) acc = fmaf(__ldg(s + D::oA + lane * NX + c), xk[c], acc);
-#pragma unroll
-            for (int i = 0; i < NU; ++i) acc = fmaf(__ldg(s + D::oB + lane * NU + i), u[i], acc);
-            w.xr()[(k + 1) * NX + lane] = acc;
-        }
-        __syncwarp();
+        rollout_step<D>(w, s, k);
     }
 }
 
 // Forward rollout of given (scaled) inputs ur (one warp).
 template <class D>
 __device__ void warp_rollout(const WCtx<D>& w) {
-    constexpr int NX = D::NX, NU = D::NU;
+    Prefetch<D::SREC, true> pf;
+    pf.load(w.grec(0), w.lane);
     for (int k = 0; k < w.Nh; ++k) {
-        const float* s = w.stage(k);
-        const float* xk = w.xr() + k * NX;
-        if (w.lane < NX) {
-            const float* u = w.ur() + k * NU;
-            float acc = __ldg(s + D::oE + w.lane);
-            for (int c = 0; c < NX; ++c) acc = fmaf(__ldg(s + D::oA + w.lane * NX + c), xk[c], acc);
-            for (int i = 0; i < NU; ++i) acc = fmaf(__ldg(s + D::oB + w.lane * NU + i), u[i], acc);
-            w.xr()[(k + 1) * NX + w.lane] = acc;
-        }
+        float* s = w.buf(k);
+        pf.store(s, w.lane);
         __syncwarp();
+        if (k + 1 < w.Nh) pf.load(w.grec(k + 1), w.lane);
+        rollout_step<D>(w, s, k);
     }
 }
 
@@ -404,50 +461,59 @@ __device__ float warp_certificate(const WCtx<D>& w) {
     constexpr int NX = D::NX, NU = D::NU, CD = D::CD, M = D::M, F = D::F;
     const int lane = w.lane;
     const float sig = w.sigma, isig = 1.0f / w.sigma;
+    float den = 0.0f, uinf = 0.0f;
+    // costates and the reduced gradient, stage by stage from the end
+    Prefetch<D::SREC, true> pf;
+    pf.load(w.grec(w.Nh - 1), lane);
     for (int k = w.Nh - 1; k >= 0; --k) {
-        const float* s = w.stage(k);
+        float* s = w.buf(k);
+        pf.store(s, lane);
+        __syncwarp();
+        if (k > 0) pf.load(w.grec(k - 1), lane);
         if (lane < NX) {
-            float acc = __ldg(s + D::oQ + lane) * (w.xr()[(k + 1) * NX + lane] - __ldg(s + D::oRY + lane));
+            float acc = s[D::oQ + lane] * (w.xr()[(k + 1) * NX + lane] - s[D::oRY + lane]);
             if (k + 1 < w.Nh) {
-                const float* An = w.stage(k + 1) + D::oA;
-                for (int i = 0; i < NX; ++i) acc = fmaf(__ldg(An + i * NX + lane), w.y()[(k + 1) * NX + i], acc);
+                const float* An = w.buf(k + 1) + D::oA;  // stage k+1, kept from the previous step
+#pragma unroll
+                for (int i = 0; i < NX; ++i) acc = fmaf(An[i * NX + lane], w.y()[(k + 1) * NX + i], acc);
             }
             w.y()[k * NX + lane] = acc;
         }
         __syncwarp();
+        if (lane < NU) {
+            const int e = k * NU + lane;
+            const float rdu = s[D::oR + lane] * (w.ur()[e] - s[D::oRU + lane]) * isig;
+            float bty = 0.0f;
+#pragma unroll
+            for (int r = 0; r < NX; ++r) bty = fmaf(s[D::oB + r * NU + lane], w.y()[k * NX + r], bty);
+            bty *= isig;
+            w.wv()[e] = rdu + bty;
+            den = fmaxf(den, fmaxf(fabsf(rdu), fabsf(bty)));
+            uinf = fmaxf(uinf, fabsf(w.ur()[e]) * sig);
+        }
+        __syncwarp();
     }
-    float den = 0.0f, uinf = 0.0f;
-    for (int e = lane; e < w.Nh * NU; e += 32) {
-        const int k = e / NU, i = e % NU;
-        const float* s = w.stage(k);
-        const float rdu = __ldg(s + D::oR + i) * (w.ur()[e] - __ldg(s + D::oRU + i)) * isig;
-        float bty = 0.0f;
-        for (int r = 0; r < NX; ++r) bty = fmaf(__ldg(s + D::oB + r * NU + i), w.y()[k * NX + r], bty);
-        bty *= isig;
-        w.wv()[e] = rdu + bty;
-        den = fmaxf(den, fmaxf(fabsf(rdu), fabsf(bty)));
-        uinf = fmaxf(uinf, fabsf(w.ur()[e]) * sig);
-    }
-    __syncwarp();
     den = warp_max(den);
     uinf = warp_max(uinf);
     float feas = 0.0f, stat = 0.0f, comp = 0.0f;
     for (int e = lane; e < w.Nh * D::NC; e += 32) {
         const int k = e / D::NC, q = e % D::NC;
-        const float* s = w.stage(k);
-        const float fmax = __ldg(s + D::oFM + q) * sig;
+        const float fmax = w.fms(k, q) * sig;
         const float* us = w.ur() + k * NU + q * CD;
         float u[CD], r[CD];
+#pragma unroll
         for (int i = 0; i < CD; ++i) { u[i] = us[i] * sig; r[i] = w.wv()[k * NU + q * CD + i]; }
         if (!((w.mask(k) >> q) & 1u)) {
             float mm = 0.0f;
+#pragma unroll
             for (int i = 0; i < CD; ++i) mm = fmaxf(mm, fabsf(u[i]));
             feas = fmaxf(feas, mm / (1.0f + fmax));
             continue;
         }
-        const float mu = __ldg(s + D::oMU + q);
+        const float mu = w.mu(k, q);
         float cf[M], g[F], lam[F], nrm2[F];
         const float n = u[D::NRM];
+#pragma unroll
         for (int j = 0; j < M; ++j) {
             cf[j] = cone_coef<CD>(j, mu, w.dx, w.dy);
             const float t = u[Cone<CD>::tang(j)];
@@ -459,20 +525,20 @@ __device__ float warp_certificate(const WCtx<D>& w) {
         g[2 * M + 1] = n - fmax;
         nrm2[2 * M] = nrm2[2 * M + 1] = 1.0f;
         float gmax = -INFINITY, wmax = 0.0f;
+#pragma unroll
         for (int f = 0; f < F; ++f) { lam[f] = 0.0f; gmax = fmaxf(gmax, g[f]); }
+#pragma unroll
         for (int i = 0; i < CD; ++i) wmax = fmaxf(wmax, fabsf(r[i]));
         feas = fmaxf(feas, fmaxf(gmax, 0.0f) / (1.0f + fmax));
-        for (int sweep = 0; sweep < 200; ++sweep) {
+        for (int sweep = 0; sweep < 100; ++sweep) {
             float change = 0.0f;
+#pragma unroll
             for (int f = 0; f < F; ++f) {
+                // G_f . r for face f (tangential pair j = f/2, or the two normal faces)
                 float gr;
-                int tj = 0;
-                float cj = 0.0f, sgn = 0.0f;
                 if (f < 2 * M) {
-                    tj = Cone<CD>::tang(f >> 1);
-                    cj = cf[f >> 1];
-                    sgn = (f & 1) ? -1.0f : 1.0f;
-                    gr = sgn * r[tj] - cj * r[D::NRM];
+                    const int tj = Cone<CD>::tang(f >> 1);
+                    gr = ((f & 1) ? -r[tj] : r[tj]) - cf[f >> 1] * r[D::NRM];
                 } else {
                     gr = (f == 2 * M) ? -r[D::NRM] : r[D::NRM];
                 }
@@ -480,21 +546,24 @@ __device__ float warp_certificate(const WCtx<D>& w) {
                 const float dd = nrm2[f] + g[f] * g[f];
                 const float nl = fmaxf(0.0f, lam[f] - num / dd);
                 const float dl = nl - lam[f];
-                if (dl != 0.0f) {
-                    if (f < 2 * M) {
-                        r[tj] += sgn * dl;
-                        r[D::NRM] -= cj * dl;
-                    } else {
-                        r[D::NRM] += (f == 2 * M) ? -dl : dl;
-                    }
-                    lam[f] = nl;
-                    change = fmaxf(change, fabsf(dl) * sqrtf(dd));
+                if (f < 2 * M) {
+                    const int tj = Cone<CD>::tang(f >> 1);
+                    r[tj] += (f & 1) ? -dl : dl;
+                    r[D::NRM] -= cf[f >> 1] * dl;
+                } else {
+                    r[D::NRM] += (f == 2 * M) ? -dl : dl;
                 }
+                lam[f] = nl;
+                change = fmaxf(change, fabsf(dl) * sqrtf(dd));
             }
-            if (change <= 1e-7f * wmax) break;
+            // stop once a sweep moves no multiplier by more than 1e-9 (absolute,
+            // far below the 1e-6-level residuals certified) or 1e-7 relative
+            if (change <= 1e-9f + 1e-7f * wmax) break;
         }
         float rs = 0.0f, rc = 0.0f;
+#pragma unroll
         for (int i = 0; i < CD; ++i) rs = fmaxf(rs, fabsf(r[i]));
+#pragma unroll
         for (int f = 0; f < F; ++f) rc = fmaxf(rc, fabsf(lam[f] * g[f]));
         stat = fmaxf(stat, rs);
         comp = fmaxf(comp, rc);
@@ -513,11 +582,11 @@ __device__ bool warp_refine_modes(const WCtx<D>& w, float alpha) {
     for (int e = w.lane; e < w.Nh * D::NC; e += 32) {
         const int k = e / D::NC, q = e % D::NC;
         if (!((w.mask(k) >> q) & 1u)) continue;
-        const float* s = w.stage(k);
         float a[CD], out[CD];
+#pragma unroll
         for (int i = 0; i < CD; ++i)
             a[i] = w.ur()[k * NU + q * CD + i] - alpha * w.sigma * w.wv()[k * NU + q * CD + i];
-        const uint32_t mw = project_contact<CD>(a, out, __ldg(s + D::oMU + q), __ldg(s + D::oFM + q), w.dx, w.dy);
+        const uint32_t mw = project_contact<CD>(a, out, w.mu(k, q), w.fms(k, q), w.dx, w.dy);
         if (mw != w.modes[e]) {
             changed = true;
             w.modes[e] = mw;
@@ -547,11 +616,10 @@ __device__ void warp_write_output(const WCtx<D>& w, const RoundArgs& a, int b, i
     for (int k = w.lane; k < Nv; k += 32) {
         unsigned long long bits = 0ull;
         if (ok && k < w.Nh) {
-            const float* s = w.stage(k);
             for (int q = 0; q < D::NC; ++q) {
                 if (!((w.mask(k) >> q) & 1u)) continue;
-                const float fmax = __ldg(s + D::oFM + q) * w.sigma;
-                const float mu = __ldg(s + D::oMU + q);
+                const float fmax = w.fms(k, q) * w.sigma;
+                const float mu = w.mu(k, q);
                 const float* us = w.ur() + k * NU + q * CD;
                 const float n = us[D::NRM] * w.sigma;
                 const float thr = -1e-5f * (1.0f + fmax);
@@ -607,7 +675,11 @@ __global__ void __launch_bounds__(32 * kPolishWarps) polish_kernel(RoundArgs a, 
         const uint32_t mw = gmodes[e];
         w.modes[e] = mw;
         changed |= (mw != glast[e]);
+        const int k = e / D::NC, q = e % D::NC;
+        w.sm[w.L.cmu + e] = __ldg(w.grec(k) + D::oMU + q);
+        w.sm[w.L.cfm + e] = __ldg(w.grec(k) + D::oFM + q);
     }
+    for (int k = lane; k < w.Nh; k += 32) w.sm[w.L.cmask + k] = __ldg(w.grec(k) + D::oMASK);
     changed = __any_sync(0xffffffffu, changed);
     for (int i = lane; i < NX; i += 32) w.xr()[i] = __ldg(tail + D::tXI0 + i);
     int npol = a.out_npol[b];

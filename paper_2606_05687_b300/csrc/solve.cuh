@@ -610,7 +610,7 @@ __device__ float certificate(const Ctx<D>& c) {
         float r[CD];
         float wmax = 0.0f;
         for (int i = 0; i < CD; ++i) { r[i] = w[i]; wmax = fmaxf(wmax, fabsf(w[i])); }
-        for (int sweep = 0; sweep < 200; ++sweep) {
+        for (int sweep = 0; sweep < 100; ++sweep) {
             float change = 0.0f;
             for (int f = 0; f < F; ++f) {
                 float gr;
@@ -639,7 +639,9 @@ __device__ float certificate(const Ctx<D>& c) {
                     change = fmaxf(change, fabsf(dl) * sqrtf(dd));
                 }
             }
-            if (change <= 1e-7f * wmax) break;
+            // stop once a sweep moves no multiplier by more than 1e-9 (absolute,
+            // far below the 1e-6-level residuals certified) or 1e-7 relative
+            if (change <= 1e-9f + 1e-7f * wmax) break;
         }
         float rs = 0.0f, rc = 0.0f;
         for (int i = 0; i < CD; ++i) rs = fmaxf(rs, fabsf(r[i]));
