@@ -317,7 +317,11 @@ def run_gpu(args):
     if rank != 0:
         return
     # kernels per step: pack + (round + polish) per round; rounds end once every instance is done
-    rounds = 1 + max(0, int(np.ceil((int(iters.max()) - 20) / 10.0)))
+    rounds, m1, interval = 1, 20, 10.0
+    while m1 < int(iters.max()):
+        m1 = int(min(m1 + interval, args.max_iter))
+        interval *= 2.0
+        rounds += 1
     flops = float(flops_per_solve(iters.astype(np.float64), polishes.astype(np.float64), N).sum())
     solve_avg = statistics.mean(solve_ms)
     achieved = flops / (solve_avg / 1e3) / 1e12

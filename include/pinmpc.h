@@ -77,7 +77,10 @@ typedef struct mpc_config {
     int32_t max_iter;      /* ADMM iteration cap (the paper's experiments use 200) */
     float kkt_tol;         /* certificate tolerance on the KKT residual */
     int32_t check_start;   /* first iteration at which a certificate check runs */
-    int32_t check_every;   /* iterations between checks */
+    int32_t check_every;   /* iterations between the first and second checks */
+    float check_growth;    /* each later interval is the previous one times this (>= 1): the few
+                              instances left after the first checks run more cheap ADMM
+                              iterations per polish round */
     int32_t polish;        /* 1: polish on the read-off active set before certifying;
                               0: certify the ADMM iterate itself (the plain method) */
     int32_t accel;         /* 1: fast ADMM with restart; 0: plain ADMM */
@@ -114,7 +117,8 @@ typedef struct mpc_handle mpc_handle;
 
 /* Fill *cfg with defaults for the given problem shape (rho 100, u_scale
  * 300, max_iter 1000, kkt_tol 5e-6 -- half the 1e-5 target, a margin for
- * the FP32 rounding of the certificate -- checks from iteration 20 every 10,
+ * the FP32 rounding of the certificate -- checks at iterations 20, 30, 50,
+ * 90, ... (check_every 10, check_growth 2),
  * polish on with up to 3 refinement steps of alpha 0.05, acceleration on
  * with eta 0.999, foot 0.10 x 0.05 m). */
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,

@@ -161,6 +161,7 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->kkt_tol = 5e-6f;
     cfg->check_start = 20;
     cfg->check_every = 10;
+    cfg->check_growth = 2.0f;
     cfg->polish = 1;
     cfg->accel = 1;
     cfg->restart_eta = 0.999f;
@@ -197,7 +198,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
                     c.n_contacts, c.contact_dim);
     if (c.B_max < 1 || c.N_max < 1) return fail(nullptr, MPC_ERR_INVALID_ARG, "B_max and N_max must be >= 1");
     if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||
-        c.check_every < 1 || c.check_start < 1 || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
+        c.check_every < 1 || c.check_start < 1 || !(c.check_growth >= 1.0f) || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
         !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f) || c.refine_steps < 0 ||
         !(c.refine_alpha > 0.0f))
         return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
@@ -369,8 +370,15 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     // rounds of ADMM iterations, each followed by the polish/certify kernel;
     // stop once no instance is running (host reads the counter each round)
     int m0 = 0;
+    double interval = c.check_every;
     for (;;) {
-        const int m1 = (m0 == 0) ? std::min(c.check_start, c.max_iter) : std::min(m0 + c.check_every, c.max_iter);
+        int m1;
+        if (m0 == 0) {
+            m1 = std::min(c.check_start, c.max_iter);
+        } else {
+            m1 = (int)std::min<double>((double)m0 + interval, (double)c.max_iter);
+            interval *= c.check_growth;
+        }
         r.m0 = m0;
         r.m1 = m1;
         h->shape.launch_round(r, B, round_smem, st);

@@ -56,7 +56,7 @@ struct WarpSmem {
     static constexpr int al(int x) { return (x + 3) & ~3; }
     static constexpr int oP = 0, op = al(oP + NX * NX), oS = al(op + NX), osv = al(oS + NX * NX),
                          oSA = al(osv + NX), oSB = al(oSA + NX * NX), oSe = al(oSB + NX * NU), oet = al(oSe + NX),
-                         oot = al(oet + NX), oG = al(oot + NU), og2 = al(oG + NX * NX), oL = al(og2 + NX),
+                         oot = al(oet + NX), og2 = al(oot + NU), oL = al(og2 + NX),
                          oK = al(oL + NU * NU), out = al(oK + NU * NK), obuf0 = al(out + NU),
                          obuf1 = al(obuf0 + D::SREC), oFixed = al(obuf1 + D::SREC);
     static_assert(oK % 4 == 0 && obuf0 % 4 == 0 && obuf1 % 4 == 0 && oFixed % 4 == 0, "16-byte regions");
@@ -67,8 +67,10 @@ struct WarpSmem {
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
         xr = take((N + 1) * NX);
         ur = take(N * NU);
-        y = take(N * NX);
-        wv = take(N * NU);
+        // the certificate runs after the Riccati scan: its costates reuse the
+        // factor buffer and its gradient the S/SA/SB area when they fit
+        y = (N * NX <= NU * NU) ? oL : take(N * NX);
+        wv = (N * NU <= oSe - oS) ? oS : take(N * NU);
         modes = take(N * D::NC);
         cmu = take(N * D::NC);
         cfm = take(N * D::NC);
@@ -207,7 +209,6 @@ __device__ void warp_polish(const WCtx<D>& w) {
     float* Se = sm + WS::oSe;
     float* et = sm + WS::oet;
     float* ot_s = sm + WS::oot;
-    float* G = sm + WS::oG;
     float* g2 = sm + WS::og2;
     float* Ls = sm + WS::oL;
     float* Ks = sm + WS::oK;
@@ -354,7 +355,7 @@ __device__ void warp_polish(const WCtx<D>& w) {
             }
         }
         __syncwarp();
-        // G = SA + SB K, g2 = s - Se - SB kappa
+        // G = SA + SB K (in place over SA), g2 = s - Se - SB kappa
 #pragma unroll 1
         for (int e = lane; e < NX * NX + NX; e += 32) {
             if (e < NX * NX) {
@@ -362,7 +363,7 @@ __device__ void warp_polish(const WCtx<D>& w) {
                 float acc = SA[e];
 #pragma unroll
                 for (int i = 0; i < NU; ++i) acc = fmaf(SB[r * NU + i], Ks[i * NK + c], acc);
-                G[e] = acc;
+                SA[e] = acc;
             } else {
                 const int r = e - NX * NX;
                 float acc = sv[r] - Se[r];
@@ -380,8 +381,8 @@ __device__ void warp_polish(const WCtx<D>& w) {
                 float a1 = 0.0f, a2 = 0.0f;
 #pragma unroll
                 for (int i = 0; i < NX; ++i) {
-                    a1 = fmaf(s[D::oA + i * NX + r], G[i * NX + c], a1);
-                    a2 = fmaf(s[D::oA + i * NX + c], G[i * NX + r], a2);
+                    a1 = fmaf(s[D::oA + i * NX + r], SA[i * NX + c], a1);
+                    a2 = fmaf(s[D::oA + i * NX + c], SA[i * NX + r], a2);
                 }
                 P[e] = 0.5f * (a1 + a2);
             } else {

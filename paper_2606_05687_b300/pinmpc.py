@@ -26,6 +26,7 @@ class MpcConfig(ctypes.Structure):
                 ("N_max", ctypes.c_int32), ("rho", ctypes.c_float), ("u_scale", ctypes.c_float),
                 ("max_iter", ctypes.c_int32), ("kkt_tol", ctypes.c_float),
                 ("check_start", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("check_growth", ctypes.c_float),
                 ("polish", ctypes.c_int32), ("accel", ctypes.c_int32),
                 ("restart_eta", ctypes.c_float), ("refine_steps", ctypes.c_int32),
                 ("refine_alpha", ctypes.c_float), ("foot_half_length", ctypes.c_float),
