@@ -9,7 +9,7 @@
 #include <string>
 
 #include "../../include/pinmpc.h"
-#include "polish.cuh"
+#include "polish_cta.cuh"
 
 using namespace pinmpc;
 
@@ -47,14 +47,14 @@ void launch_solve_t(const SolveArgs& a, int B, int n_rec, int smem, cudaStream_t
     solve_kernel<D><<<B, 32 * a.N, smem, s>>>(a, n_rec);
 }
 template <class D>
-int polish_smem_t(int N) { return kPolishWarps * WarpSmem<D>(N).total * 4; }
+int polish_smem_t(int N) { return CtaSmem<D>(N).total * 4; }
 template <class D>
 int state_floats_t(int N) { return RoundState<D>::floats(N); }
 template <class D>
 cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
     cudaError_t e = cudaFuncSetAttribute(round_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(polish_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
+    return cudaFuncSetAttribute(polish_cta_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
 }
 template <class D>
 void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
@@ -62,7 +62,7 @@ void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
 }
 template <class D>
 void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
-    polish_kernel<D><<<(B + kPolishWarps - 1) / kPolishWarps, 32 * kPolishWarps, smem, s>>>(a, B);
+    polish_cta_kernel<D><<<B, kPT, smem, s>>>(a);
 }
 template <class D>
 Shape make_shape() {

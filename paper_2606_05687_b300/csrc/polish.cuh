@@ -129,8 +129,8 @@ struct WCtx {
 // Column i of the reduced input map of one stage (lane i < NU), from the
 // stage's record s in shared memory:
 // bt = Bs T e_i, rt = (T'RsT)_ii (1 for an eliminated column), gt = (T'Rs(o - rus))_i, ot = o_i.
-template <class D>
-__device__ __forceinline__ void reduced_column(const WCtx<D>& w, const float* s, uint32_t mw, int i, float* bt,
+template <class D, class C>
+__device__ __forceinline__ void reduced_column(const C& w, const float* s, uint32_t mw, int i, float* bt,
                                                float& rt, float& gt, float& ot) {
     constexpr int NX = D::NX, NU = D::NU, CD = D::CD;
     const int q = i / CD, j = i % CD, base = q * CD;
