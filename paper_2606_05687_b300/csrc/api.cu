@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/pinmpc.h"
+#include "admm.cuh"
 #include "polish_cta.cuh"
 
 using namespace pinmpc;
@@ -52,13 +53,17 @@ template <class D>
 int state_floats_t(int N) { return RoundState<D>::floats(N); }
 template <class D>
 cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(round_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    cudaError_t e = cudaFuncSetAttribute(round2_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(round2_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(polish_cta_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
 }
 template <class D>
 void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
-    round_kernel<D><<<B, 32 * a.N, smem, s>>>(a);
+    // register-heavy form for up to 20 stages (640 threads), 64-register form above
+    if (a.N <= 20) round2_kernel<D, 640><<<B, 32 * a.N, smem, s>>>(a);
+    else round2_kernel<D, 1024><<<B, 32 * a.N, smem, s>>>(a);
 }
 template <class D>
 void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {

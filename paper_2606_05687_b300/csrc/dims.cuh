@@ -27,7 +27,10 @@ struct Dims {
     static constexpr int CD = CD_;
     static constexpr int NC = NU_ / CD_;          // contacts per stage
     static constexpr int NB = NX + NU;            // lifted dimension nbar = nx + nu
-    static constexpr int NBP = (NB + 3) & ~3;     // padded vector stride
+    // row split of the register-resident ADMM products: a row of T = [A B] is
+    // held by two lanes, columns [0, CS) and [CS, 2 CS) (zero beyond NB)
+    static constexpr int CS = (((NB + 1) / 2) + 3) & ~3;
+    static constexpr int NBP = ((NB + 3) & ~3) > 2 * CS ? ((NB + 3) & ~3) : 2 * CS;  // padded vector stride
     static constexpr int M = Cone<CD>::M;         // tangential components per contact
     static constexpr int F = 2 * M + 2;           // faces per contact
     static constexpr int NRM = 2;                 // normal component index
