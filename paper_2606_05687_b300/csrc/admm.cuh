@@ -1,28 +1,52 @@
-// ADMM round kernel with register-resident stage matrices.
+// ADMM round kernel: one CTA per instance, one warp per stage.
 //
-// Same iteration as block1/block2 in solve.cuh (Sec. III, the closed-form
-// horizon-parallel updates in the factored form described there), one CTA
-// per instance and one warp per stage, but each warp keeps its stage's
-// T_j = [A_j B_j], S_j and W_j in registers in two layouts:
+// The iteration is the three-block ADMM of Sec. III with its closed-form,
+// horizon-parallel updates, in the factored form
+//   J_j g = g - B_j' S_j B_j g,            S_j = (I + B_j B_j')^{-1}
+//   H h   = D'^{-1}(h - T' W_j T D'^{-1} h), W_j = (I/rho + T D'^{-1} T')^{-1}
+// with T = T_j = [A_j B_j] and D' the diagonal of the previous stage's cost
+// plus the penalties.  Warp j keeps T_j in registers in two layouts:
 //   column layout: lane c holds column c (and 32 + c) of T   -> T' x products
-//   row layout:    lanes 2r, 2r+1 hold halves of row r of T,
-//                  S and W                                   -> T x, S x, W x
-// so every product is a short register dot product over vectors read from
-// shared memory as broadcast float4, plus one shuffle for the row halves.
-// The Nesterov-extrapolated values are formed where they are read.
+//   row layout:    lanes 2r, 2r+1 hold halves of row r of T  -> T x products
+// S_j and W_j stay in shared memory as 16-float padded rows.  Everything
+// that only stage j reads (its extrapolated iterate, B du_j, Abar_j xibar_j,
+// its constants) lives in the registers of element lanes i and 32 + i, so a
+// stage-iteration touches shared memory only for the vectors other lanes or
+// other stages read.
 #pragma once
 #include "polish.cuh"
 
 namespace pinmpc {
 
 template <class D>
+struct RoundSmem {
+    static constexpr int kTmp = 5;  // per-warp scratch vectors
+    static constexpr int FR = 16;   // padded row length of S_j and W_j
+    int sd, var, xb, tmp, pre, fac, part, total;
+    __host__ __device__ explicit RoundSmem(int N) {
+        int o = 0;
+        auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
+        sd = take(N * D::SREC);
+        var = take(RoundState<D>::var_floats(N));
+        xb = take((N + 1) * D::NBP);
+        tmp = take(N * kTmp * D::NBP);
+        pre = take(N * 3 * D::NBP);
+        fac = take(N * 2 * D::NX * FR);
+        part = take(32);
+        total = o;
+    }
+    __host__ __device__ int bytes() const { return total * 4; }
+    // floats of the per-instance factor cache (S_j, W_j for every stage)
+    __host__ __device__ static int cache_floats(int N) { return N * 2 * D::NX * FR; }
+};
+
+template <class D>
 struct RegT {
-    static constexpr int NX = D::NX, NB = D::NB, CS = D::CS, SS = 8;
-    float colA[NX];  // column lane of T
-    float colB[NX];  // column 32 + lane of T (0 where it does not exist)
-    float rowT[CS];  // row lane/2 of T, columns [(lane&1) CS, (lane&1) CS + CS)
-    float rowS[SS];  // row lane/2 of S_j, columns [(lane&1) 8, ... + 8)
-    float rowW[SS];  // row lane/2 of W_j
+    static constexpr int NX = D::NX, NB = D::NB, CS = D::CS;
+    static constexpr bool kTwo = NB > 32;  // some columns live in a second lane slot
+    float colA[NX];                        // column lane of T
+    float colB[kTwo ? NX : 1];             // column 32 + lane of T (0 where it does not exist)
+    float rowT[CS];                        // row lane/2 of T, columns [(lane&1) CS, (lane&1) CS + CS)
     static_assert(NX <= 16, "row split of S and W assumes nx <= 16");
 };
 
@@ -43,22 +67,23 @@ __device__ __forceinline__ float prod_T(const RegT<D>& M, const float* x, int la
     return acc + __shfl_xor_sync(0xffffffffu, acc, 1);
 }
 
-// y_r = sum_c R[r][c] x[c] for R = S_j or W_j (rows split 8 + 8); x has finite padding to 16.
-__device__ __forceinline__ float prod_R(const float (&row)[8], const float* x, int lane) {
+// y_r = sum_c R[r][c] x[c] for a 16-float padded row (R = S_j or W_j); x has finite padding to 16.
+__device__ __forceinline__ float prod_R(const float* row, const float* x, int lane) {
+    const float4* m4 = reinterpret_cast<const float4*>(row + (lane & 1) * 8);
     const float4* x4 = reinterpret_cast<const float4*>(x + (lane & 1) * 8);
-    const float4 v0 = x4[0], v1 = x4[1];
-    float a0 = row[0] * v0.x, a1 = row[1] * v0.y;
-    a0 = fmaf(row[2], v0.z, a0);
-    a1 = fmaf(row[3], v0.w, a1);
-    a0 = fmaf(row[4], v1.x, a0);
-    a1 = fmaf(row[5], v1.y, a1);
-    a0 = fmaf(row[6], v1.z, a0);
-    a1 = fmaf(row[7], v1.w, a1);
+    const float4 r0 = m4[0], r1 = m4[1], v0 = x4[0], v1 = x4[1];
+    float a0 = r0.x * v0.x, a1 = r0.y * v0.y;
+    a0 = fmaf(r0.z, v0.z, a0);
+    a1 = fmaf(r0.w, v0.w, a1);
+    a0 = fmaf(r1.x, v1.x, a0);
+    a1 = fmaf(r1.y, v1.y, a1);
+    a0 = fmaf(r1.z, v1.z, a0);
+    a1 = fmaf(r1.w, v1.w, a1);
     const float acc = a0 + a1;
     return acc + __shfl_xor_sync(0xffffffffu, acc, 1);
 }
 
-// (y_lane, y_{32+lane}) with y_c = sum_r T[r][c] x[r]; x holds NX entries.
+// (y_lane, y_{32+lane}) with y_c = sum_r T[r][c] x[r]; x holds NX entries (finite padding to 4).
 template <class D>
 __device__ __forceinline__ float2 prod_Tt(const RegT<D>& M, const float* x) {
     constexpr int NX = D::NX;
@@ -73,7 +98,7 @@ __device__ __forceinline__ float2 prod_Tt(const RegT<D>& M, const float* x) {
             const int r = 4 * q + t;
             if (r < NX) {
                 a0 = fmaf(M.colA[r], xv[t], a0);
-                a1 = fmaf(M.colB[r], xv[t], a1);
+                if constexpr (RegT<D>::kTwo) a1 = fmaf(M.colB[r], xv[t], a1);
             }
         }
     }
@@ -84,302 +109,344 @@ __device__ __forceinline__ float2 prod_Tt(const RegT<D>& M, const float* x) {
 enum : int { PQB = 0, PID = 1, PIDN = 2 };
 
 template <class D>
-struct Ctx2 {
-    float *var, *xb, *ax, *bdu, *tmp, *pre, *sd, *part;
-    uint32_t* modes;
+struct RCtx {
+    float *var, *xb, *tmp, *pre, *fac, *part;
     int N, Nh;
-    float rho, dx, dy, wgt;
-    bool restart;
-    int cb;
-    __device__ const float* stage(int k) const { return sd + k * D::SREC; }
-    __device__ float* V(int buf, int which, int j) const { return var + ((buf * 5 + which) * N + j) * D::NBP; }
-    __device__ float* T(int j, int t) const { return tmp + (j * Smem<D>::kTmpVecs + t) * D::NBP; }
-    __device__ float* P(int j, int t) const { return pre + (j * 3 + t) * D::NBP; }
-    __device__ uint32_t mask(int k) const { return __float_as_uint(stage(k)[D::oMASK]); }
-    // extrapolated (hatted) value of variable `which` of stage j, element i
-    __device__ float hat(int which, int j, int i) const {
-        const float c = V(cb, which, j)[i], p = V(1 - cb, which, j)[i];
-        return restart ? p : fmaf(wgt, c - p, c);
+    float rho;
+    __device__ float* T(int j, int t) const { return tmp + (j * RoundSmem<D>::kTmp + t) * D::NBP; }
+    __device__ const float* P(int j, int t) const { return pre + (j * 3 + t) * D::NBP; }
+    // padded row min(lane/2, NX-1) of S_j (m = 0) or W_j (m = 1)
+    __device__ const float* Frow(int j, int m, int lane) const {
+        const int r = min(lane >> 1, D::NX - 1);
+        return fac + ((j * 2 + m) * D::NX + r) * RoundSmem<D>::FR;
     }
 };
 
-// Block 1 of stage j (warp j): du_j (B du into bdu[0, NX), du into bdu[NX, NB)),
-// xibar_j = H_{j-1} htilde_{j-1} (factored), Abar_j xibar_j, and xibar_N for the last stage.
+// Registers of warp j: element slots i = lane (s = 0) and i = 32 + lane (s = 1).
 template <class D>
-__device__ void block1_reg(const Ctx2<D>& c, const RegT<D>& M, int j, int lane) {
-    constexpr int NX = D::NX, NB = D::NB;
+struct StageRegs {
+    float e0;                 // ebar_j[lane] (0 beyond NX)
+    float qbp[2], idp[2];     // qbar_{j-1} and 1/D'_{j-1}
+    float mu, fmx;            // contact lane q: friction coefficient and force bound
+    uint32_t stance;          // contact lane q is in stance
+    uint32_t mw;              // contact lane q: faces of the latest projection
+    float ax[2];              // Abar_j xibar_j
+    float bd[2];              // B_j du_j (state rows) and du_j (input rows)
+    float zh[2], vh[2], thh[2], beh[2], lah[2];  // extrapolated iterate of stage j
+};
+
+// Extrapolated value fma(wa, current, wb * previous) of variable `which`
+// at element i: wa = 1 + w, wb = -w for Nesterov weight w; wa = 0, wb = 1 on
+// a restart (the previous iterate).
+__device__ __forceinline__ float hat_at(const float* cur, const float* prv, int off, float wa, float wb) {
+    return fmaf(wa, cur[off], wb * prv[off]);
+}
+
+template <class D>
+__device__ __forceinline__ void load_hats(const RCtx<D>& c, StageRegs<D>& R, int cb, int j, int lane, float wa,
+                                          float wb) {
+    constexpr int NBP = D::NBP, NB = D::NB;
+    const float* cur = c.var + RoundState<D>::at(c.N, cb, j, 0);
+    const float* prv = c.var + RoundState<D>::at(c.N, 1 - cb, j, 0);
+    const bool v0 = lane < NB;
+    R.zh[0] = v0 ? hat_at(cur, prv, VZ * NBP + lane, wa, wb) : 0.0f;
+    R.vh[0] = v0 ? hat_at(cur, prv, VV * NBP + lane, wa, wb) : 0.0f;
+    R.thh[0] = v0 ? hat_at(cur, prv, VTH * NBP + lane, wa, wb) : 0.0f;
+    R.beh[0] = v0 ? hat_at(cur, prv, VBE * NBP + lane, wa, wb) : 0.0f;
+    R.lah[0] = v0 ? hat_at(cur, prv, VLA * NBP + lane, wa, wb) : 0.0f;
+    if constexpr (RegT<D>::kTwo) {
+        const bool v1 = lane < NB - 32;
+        const int i = 32 + lane;
+        R.zh[1] = v1 ? hat_at(cur, prv, VZ * NBP + i, wa, wb) : 0.0f;
+        R.vh[1] = v1 ? hat_at(cur, prv, VV * NBP + i, wa, wb) : 0.0f;
+        R.thh[1] = v1 ? hat_at(cur, prv, VTH * NBP + i, wa, wb) : 0.0f;
+        R.beh[1] = v1 ? hat_at(cur, prv, VBE * NBP + i, wa, wb) : 0.0f;
+        R.lah[1] = v1 ? hat_at(cur, prv, VLA * NBP + i, wa, wb) : 0.0f;
+    } else {
+        R.zh[1] = R.vh[1] = R.thh[1] = R.beh[1] = R.lah[1] = 0.0f;
+    }
+}
+
+// Block 1 of stage j (warp j): du_j, xibar_j = H_{j-1} htilde_{j-1} (factored),
+// Abar_j xibar_j, and xibar_N for the last stage.
+template <class D>
+__device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, StageRegs<D>& R, int cb, int j,
+                                         int lane, float wa, float wb) {
+    constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP;
+    constexpr bool TWO = RegT<D>::kTwo;
     const float rho = c.rho;
-    const int r = lane >> 1, h = lane & 1;
-    const bool rowlane = (r < NX) && (h == 0);
+    const int r = lane >> 1;
+    const bool rowlane = (r < NX) && !(lane & 1);
+    const bool v0 = lane < NB, v1 = TWO && lane < NB - 32, p1 = TWO && lane < NBP - 32;
     float* om = c.T(j, 0);
     float* gv = c.T(j, 1);
     float* pv = c.T(j, 2);
     float* sv = c.T(j, 3);
-    float* bdu = c.bdu + j * D::NBP;
-    const int c0 = lane, c1 = 32 + lane;
-    // omega = vhat - betahat
-    for (int i = lane; i < NB; i += 32) om[i] = c.hat(VV, j, i) - c.hat(VBE, j, i);
+    float* cp = c.T(j, 4);
+    // omega = vhat - betahat; T' omega reads its first NX (padded to 4) entries
+    const float om0 = R.vh[0] - R.beh[0], om1 = R.vh[1] - R.beh[1];
+    if (lane < ((NX + 3) & ~3)) om[lane] = om0;
     __syncwarp();
     // g = B' omega_x + omega_u on the input columns (0 on the state columns)
     const float2 tg = prod_Tt<D>(M, om);
-    const float g0 = (c0 >= NX && c0 < NB) ? tg.x + om[c0] : 0.0f;
-    const float g1 = (c1 < NB) ? tg.y + om[c1] : 0.0f;
-    if (c0 < NB) gv[c0] = g0;
-    if (c1 < NB) gv[c1] = g1;
+    const float g0 = (lane >= NX && v0) ? tg.x + om0 : 0.0f;
+    const float g1 = v1 ? tg.y + om1 : 0.0f;
+    gv[lane] = g0;
+    if (p1) gv[32 + lane] = g1;
     __syncwarp();
-    // p = B g ; s = S p (= B du)
+    // p = B g ; s = S p (= B du) ; du = g - B' s
     const float pr = prod_T<D>(M, gv, lane);
     if (rowlane) pv[r] = pr;
     __syncwarp();
-    const float sr = prod_R(M.rowS, pv, lane);
-    if (rowlane) {
-        sv[r] = sr;
-        bdu[r] = sr;
-    }
+    const float sr = prod_R(c.Frow(j, 0, lane), pv, lane);
+    if (rowlane) sv[r] = sr;
     __syncwarp();
-    // du = g - B' s
     const float2 bs = prod_Tt<D>(M, sv);
-    if (c0 >= NX && c0 < NB) bdu[c0] = g0 - bs.x;
-    if (c1 < NB) bdu[c1] = g1 - bs.y;
+    const float sx = __shfl_sync(0xffffffffu, sr, (2 * lane) & 31);
+    R.bd[0] = lane < NX ? sx : g0 - bs.x;
+    R.bd[1] = g1 - bs.y;
     if (j >= 1) {
-        float* wx = c.T(j, 4);
-        float* cp = c.T(j, 5);
-        const float* sj = c.stage(j);
-        const float* qb = c.P(j - 1, PQB);
-        const float* idp = c.P(j - 1, PID);
-        // w = zhat_{j+1} - vhat_j - ebar_j + lambdahat_j ; c' = D'^{-1}(qbar + rho(zhat_j - thetahat_{j-1}) + rho [0; w_u])
-        for (int i = lane; i < NB; i += 32) {
-            const float wi = c.hat(VZ, j, i) - c.hat(VV, j, i) - (i < NX ? sj[D::oE + i] : 0.0f) + c.hat(VLA, j, i);
-            float cc = qb[i] + rho * (c.hat(VZ, j - 1, i) - c.hat(VTH, j - 1, i));
-            if (i >= NX) cc = fmaf(rho, wi, cc);
-            else wx[i] = wi;
-            cp[i] = cc * idp[i];
+        // w = zhat_j - vhat_j - ebar_j + lambdahat_j ;
+        // c' = D'^{-1}(qbar + rho (zhat_{j-1} - thetahat_{j-1}) + rho [0; w_u])
+        const float* cur = c.var + RoundState<D>::at(c.N, cb, j - 1, 0);
+        const float* prv = c.var + RoundState<D>::at(c.N, 1 - cb, j - 1, 0);
+        const float w0 = R.zh[0] - R.vh[0] - R.e0 + R.lah[0];
+        float cc0 = 0.0f, cc1 = 0.0f;
+        if (v0) {
+            cc0 = fmaf(rho, hat_at(cur, prv, VZ * NBP + lane, wa, wb) - hat_at(cur, prv, VTH * NBP + lane, wa, wb),
+                       R.qbp[0]);
+            if (lane >= NX) cc0 = fmaf(rho, w0, cc0);
         }
+        if (v1) {
+            const float w1 = R.zh[1] - R.vh[1] + R.lah[1];
+            cc1 = fmaf(rho, hat_at(cur, prv, VZ * NBP + 32 + lane, wa, wb) - hat_at(cur, prv, VTH * NBP + 32 + lane, wa, wb),
+                       R.qbp[1]);
+            cc1 = fmaf(rho, w1, cc1);
+        }
+        const float cp0 = cc0 * R.idp[0], cp1 = cc1 * R.idp[1];
+        cp[lane] = cp0;
+        if (p1) cp[32 + lane] = cp1;
         __syncwarp();
         // t = T c' - w_x ; sigma = W t
-        const float tr = prod_T<D>(M, cp, lane) - ((r < NX) ? wx[r] : 0.0f);
-        __syncwarp();
+        const float wx = __shfl_sync(0xffffffffu, w0, r & 31);
+        const float tr = prod_T<D>(M, cp, lane) - wx;
         if (rowlane) pv[r] = tr;
         __syncwarp();
-        const float sg = prod_R(M.rowW, pv, lane);
-        __syncwarp();
+        const float sg = prod_R(c.Frow(j, 1, lane), pv, lane);
         if (rowlane) om[r] = sg;
         __syncwarp();
         // xibar_j = c' - D'^{-1} T' sigma
         const float2 ts = prod_Tt<D>(M, om);
-        float* xbj = c.xb + j * D::NBP;
-        if (c0 < NB) xbj[c0] = fmaf(-idp[c0], ts.x, cp[c0]);
-        if (c1 < NB) xbj[c1] = fmaf(-idp[c1], ts.y, cp[c1]);
+        const float xb0 = v0 ? fmaf(-R.idp[0], ts.x, cp0) : 0.0f;
+        const float xb1 = v1 ? fmaf(-R.idp[1], ts.y, cp1) : 0.0f;
+        float* xbj = c.xb + j * NBP;
+        xbj[lane] = xb0;
+        if (p1) xbj[32 + lane] = xb1;
         __syncwarp();
         // Abar_j xibar_j
         const float ar = prod_T<D>(M, xbj, lane);
-        float* axj = c.ax + j * D::NBP;
-        if (rowlane) axj[r] = ar;
-        if (c0 >= NX && c0 < NB) axj[c0] = xbj[c0];
-        if (c1 < NB) axj[c1] = xbj[c1];
+        const float axs = __shfl_sync(0xffffffffu, ar, (2 * lane) & 31);
+        R.ax[0] = lane < NX ? axs : xb0;
+        R.ax[1] = xb1;
     }
     if (j == c.Nh - 1) {
-        float* xbN = c.xb + c.Nh * D::NBP;
+        float* xbN = c.xb + c.Nh * NBP;
         const float* qb = c.P(j, PQB);
         const float* idn = c.P(j, PIDN);
-        for (int i = lane; i < NB; i += 32)
-            xbN[i] = (qb[i] + rho * (c.hat(VZ, j, i) - c.hat(VTH, j, i))) * idn[i];
+        xbN[lane] = v0 ? fmaf(rho, R.zh[0] - R.thh[0], qb[lane]) * idn[lane] : 0.0f;
+        if (p1) xbN[32 + lane] = v1 ? fmaf(rho, R.zh[1] - R.thh[1], qb[32 + lane]) * idn[32 + lane] : 0.0f;
     }
-    __syncwarp();
 }
 
 // Block 2 and the dual ascents of stage j; new values go to buffer 1 - cb.
+// Returns the stage's share of the combined residual (valid in every lane).
 template <class D>
-__device__ void block2_reg(const Ctx2<D>& c, int j, int lane) {
-    constexpr int NX = D::NX, NB = D::NB, CD = D::CD;
-    const int nb = 1 - c.cb;
-    const float* sj = c.stage(j);
-    const float* xbn = c.xb + (j + 1) * D::NBP;
-    const float* axj = c.ax + j * D::NBP;
-    const float* bdu = c.bdu + j * D::NBP;
+__device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int cb, int j, int lane, float dx,
+                                          float dy) {
+    constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP, CD = D::CD;
+    constexpr bool TWO = RegT<D>::kTwo;
+    const bool v0 = lane < NB, v1 = TWO && lane < NB - 32;
+    const float* xbn = c.xb + (j + 1) * NBP;
     float* arg = c.T(j, 0);
     float* zp = c.T(j, 1);
-    float zh[2], vh[2], th[2], bh[2], lh[2], gam[2];
-#pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-        const int i = lane + 32 * s2;
-        if (i < NB) {
-            zh[s2] = c.hat(VZ, j, i);
-            vh[s2] = c.hat(VV, j, i);
-            th[s2] = c.hat(VTH, j, i);
-            bh[s2] = c.hat(VBE, j, i);
-            lh[s2] = c.hat(VLA, j, i);
-            const float eb = i < NX ? sj[D::oE + i] : 0.0f;
-            const float g_ = bdu[i] + bh[s2] - axj[i] - eb + lh[s2];
-            const float gt_ = xbn[i] + th[s2] + axj[i] + eb - lh[s2];
-            arg[i] = (2.0f * gt_ + g_) * (1.0f / 3.0f);
-            gam[s2] = g_;
-        } else {
-            zh[s2] = vh[s2] = th[s2] = bh[s2] = lh[s2] = gam[s2] = 0.0f;
-        }
-    }
+    // gamma = B du + betahat - Abar xibar - ebar + lambdahat ; gammatilde = xibar_{j+1} + thetahat + Abar xibar + ebar - lambdahat
+    const float xn0 = v0 ? xbn[lane] : 0.0f;
+    const float xn1 = v1 ? xbn[32 + lane] : 0.0f;
+    const float ga0 = R.bd[0] + R.beh[0] - R.ax[0] - R.e0 + R.lah[0];
+    const float gt0 = xn0 + R.thh[0] + R.ax[0] + R.e0 - R.lah[0];
+    const float a0 = (2.0f * gt0 + ga0) * (1.0f / 3.0f);
+    const float ga1 = R.bd[1] + R.beh[1] - R.ax[1] + R.lah[1];
+    const float gt1 = xn1 + R.thh[1] + R.ax[1] - R.lah[1];
+    const float a1 = (2.0f * gt1 + ga1) * (1.0f / 3.0f);
+    if (v0) arg[lane] = a0;
+    if (v1) arg[32 + lane] = a1;
     __syncwarp();
-    if (lane < NX) zp[lane] = arg[lane];
     if (lane < D::NC) {
         const int q = lane;
-        uint32_t mw;
-        if ((c.mask(j) >> q) & 1u) {
-            mw = project_contact<CD>(arg + NX + q * CD, zp + NX + q * CD, sj[D::oMU + q], sj[D::oFM + q], c.dx, c.dy);
+        if (R.stance) {
+            R.mw = project_contact<CD>(arg + NX + q * CD, zp + NX + q * CD, R.mu, R.fmx, dx, dy);
         } else {
+#pragma unroll
             for (int i = 0; i < CD; ++i) zp[NX + q * CD + i] = 0.0f;
-            mw = kSwingBit;
+            R.mw = kSwingBit;
         }
-        c.modes[j * D::NC + q] = mw;
     }
     __syncwarp();
-    float* zn = c.V(nb, VZ, j);
-    float* vn = c.V(nb, VV, j);
-    float* tn = c.V(nb, VTH, j);
-    float* bn = c.V(nb, VBE, j);
-    float* ln = c.V(nb, VLA, j);
+    float* nxt = c.var + RoundState<D>::at(c.N, 1 - cb, j, 0);
     float cm = 0.0f;
-#pragma unroll
-    for (int s2 = 0; s2 < 2; ++s2) {
-        const int i = lane + 32 * s2;
-        if (i < NB) {
-            const float eb = i < NX ? sj[D::oE + i] : 0.0f;
-            const float z = zp[i];
-            const float v = 0.5f * (z + gam[s2]);
-            const float th_ = th[s2] + xbn[i] - z;
-            const float be_ = bh[s2] + bdu[i] - v;
-            const float la_ = lh[s2] + z - axj[i] - v - eb;
-            zn[i] = z;
-            vn[i] = v;
-            tn[i] = th_;
-            bn[i] = be_;
-            ln[i] = la_;
-            const float d1 = th_ - th[s2], d2 = be_ - bh[s2], d3 = la_ - lh[s2];
-            const float d4 = z - zh[s2], d5 = v - vh[s2], d6 = d4 - d5;
-            cm += d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5 + d6 * d6;
-        }
+    if (v0) {
+        const float z = lane < NX ? a0 : zp[lane];
+        const float v = 0.5f * (z + ga0);
+        const float th = R.thh[0] + xn0 - z;
+        const float be = R.beh[0] + R.bd[0] - v;
+        const float la = R.lah[0] + z - R.ax[0] - v - R.e0;
+        nxt[VZ * NBP + lane] = z;
+        nxt[VV * NBP + lane] = v;
+        nxt[VTH * NBP + lane] = th;
+        nxt[VBE * NBP + lane] = be;
+        nxt[VLA * NBP + lane] = la;
+        const float d1 = th - R.thh[0], d2 = be - R.beh[0], d3 = la - R.lah[0];
+        const float d4 = z - R.zh[0], d5 = v - R.vh[0], d6 = d4 - d5;
+        cm = d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5 + d6 * d6;
     }
-    cm = warp_sum(cm);
-    if (lane == 0) c.part[j] = cm;
+    if (v1) {
+        const int i = 32 + lane;
+        const float z = zp[i];
+        const float v = 0.5f * (z + ga1);
+        const float th = R.thh[1] + xn1 - z;
+        const float be = R.beh[1] + R.bd[1] - v;
+        const float la = R.lah[1] + z - R.ax[1] - v;
+        nxt[VZ * NBP + i] = z;
+        nxt[VV * NBP + i] = v;
+        nxt[VTH * NBP + i] = th;
+        nxt[VBE * NBP + i] = be;
+        nxt[VLA * NBP + i] = la;
+        const float d1 = th - R.thh[1], d2 = be - R.beh[1], d3 = la - R.lah[1];
+        const float d4 = z - R.zh[1], d5 = v - R.vh[1], d6 = d4 - d5;
+        cm += d1 * d1 + d2 * d2 + d3 * d3 + d4 * d4 + d5 * d5 + d6 * d6;
+    }
+    return warp_sum(cm);
 }
 
-// One round of ADMM iterations (CTA per instance, warp per stage) with the
-// caches and the iterate kept in global memory between rounds.
+// Row r of  dg I + T diag(d) T'  over the columns i >= i0 of T = [A B] (lane
+// pair (r, h) sums the columns i = i0 + h, i0 + h + 2, ...; the pair's halves
+// are combined), then its in-place Gauss-Jordan inverse (no pivoting: the
+// matrix is SPD).  Rows are held one per lane pair; lanes past the last row
+// duplicate it.
+template <class D>
+__device__ __forceinline__ void gram_inverse(const float* sj, const float* d, float dg, int i0, int lane,
+                                             float (&row)[D::NX]) {
+    constexpr int NX = D::NX, NU = D::NU, NB = D::NB;
+    const int r = min(lane >> 1, NX - 1), h = lane & 1;
+#pragma unroll
+    for (int cc = 0; cc < NX; ++cc) row[cc] = 0.0f;
+#pragma unroll 2
+    for (int i = i0 + h; i < NB; i += 2) {
+        const float* col = i < NX ? sj + D::oA + i : sj + D::oB + (i - NX);
+        const int stride = i < NX ? NX : NU;
+        const float tri = col[r * stride] * (d ? d[i] : 1.0f);
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) row[cc] = fmaf(tri, col[cc * stride], row[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < NX; ++cc) {
+        row[cc] += __shfl_xor_sync(0xffffffffu, row[cc], 1);
+        if (cc == r) row[cc] += dg;
+    }
+#pragma unroll
+    for (int p = 0; p < NX; ++p) {
+        float prow[NX];
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) prow[cc] = __shfl_sync(0xffffffffu, row[cc], 2 * p);
+        const float piv = 1.0f / prow[p];
+        const float fp = row[p] * piv;
+        const bool mine = (r == p);
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) {
+            const float other = (cc == p) ? -fp : fmaf(-fp, prow[cc], row[cc]);
+            const float pivr = (cc == p) ? piv : prow[cc] * piv;
+            row[cc] = mine ? pivr : other;
+        }
+    }
+}
+
+// Writes a failure status for instance b (no iterate): zero trajectory and inputs.
+template <class D>
+__device__ void round_fail(const RoundArgs& a, int b, int status) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int e = tid; e < a.N * D::NX; e += nthr) a.out_xi[(size_t)b * a.N * D::NX + e] = 0.0f;
+    for (int e = tid; e < a.N * D::NU; e += nthr) a.out_u[(size_t)b * a.N * D::NU + e] = 0.0f;
+    for (int k = tid; k < a.N; k += nthr) a.out_bits[(size_t)b * a.N + k] = 0ull;
+    if (tid == 0) {
+        a.out_status[b] = status;
+        a.out_iters[b] = 0;
+        a.out_kkt[b] = INFINITY;
+        a.out_npol[b] = 0;
+        a.done[b] = 1;
+    }
+}
+
+// One round of ADMM iterations (a.m0, a.m1] for one instance per CTA; the
+// factor cache and the iterate stay in global memory between rounds.
 template <class D, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
-    constexpr int NX = D::NX, NU = D::NU, NB = D::NB;
+    constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
+    constexpr bool TWO = RegT<D>::kTwo;
     const int b = blockIdx.x;
     if (a.done[b]) return;
-    const Smem<D> L(a.N);
-    Ctx<D> c;  // setup helpers (records, caches)
-    c.sd = smem + L.sd; c.Sm = smem + L.Sm; c.Wm = smem + L.Wm; c.var = smem + L.var;
-    c.hat = smem + L.hat; c.xb = smem + L.xb; c.ax = smem + L.ax; c.bdu = smem + L.bdu;
-    c.tmp = smem + L.tmp; c.Kst = smem + L.Kst; c.wk = smem + L.wk; c.xr = smem + L.xr;
-    c.ur = smem + L.ur; c.y = smem + L.y; c.wv = smem + L.wv; c.red = smem + L.red;
-    c.part = smem + L.part; c.res = smem + L.res;
-    c.modes = reinterpret_cast<uint32_t*>(smem + L.modes);
-    c.lastm = reinterpret_cast<uint32_t*>(smem + L.lastm);
-    c.N = a.N;
-    c.rho = a.rho; c.sigma = a.sigma; c.dx = a.dx; c.dy = a.dy;
+    const RoundSmem<D> L(a.N);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const float* rec = a.rec + (size_t)b * a.irec;
     const float* tail = rec + (size_t)a.n_rec * D::SREC;
-    const int Nh = __float_as_int(tail[D::tH]);
-    c.Nh = (Nh >= 1 && Nh <= a.N) ? Nh : 0;
-    SolveArgs wa{};
-    wa.N = a.N; wa.out_xi = a.out_xi; wa.out_u = a.out_u; wa.out_status = a.out_status;
-    wa.out_iters = a.out_iters; wa.out_kkt = a.out_kkt; wa.out_bits = a.out_bits; wa.out_npol = a.out_npol;
-    if (c.Nh == 0) {
-        write_output<D>(c, wa, b, kBadHorizon, 0, 0.0f, 0);
-        if (tid == 0) a.done[b] = 1;
+    const int Nh0 = __float_as_int(__ldg(tail + D::tH));
+    const int Nh = (Nh0 >= 1 && Nh0 <= a.N) ? Nh0 : 0;
+    if (Nh == 0) {
+        round_fail<D>(a, b, kBadHorizon);
         return;
     }
+    RCtx<D> c;
+    c.var = smem + L.var; c.xb = smem + L.xb; c.tmp = smem + L.tmp; c.pre = smem + L.pre;
+    c.fac = smem + L.fac; c.part = smem + L.part;
+    c.N = a.N; c.Nh = Nh; c.rho = a.rho;
+    float* sd = smem + L.sd;
     {
         const float4* src = reinterpret_cast<const float4*>(rec);
-        float4* dst = reinterpret_cast<float4*>(c.sd);
-        const int n4 = c.Nh * D::SREC / 4;
-        for (int e = tid; e < n4; e += nthr) dst[e] = src[e];
+        float4* dst = reinterpret_cast<float4*>(sd);
+        const int n4 = Nh * D::SREC / 4;
+        for (int e = tid; e < n4; e += nthr) dst[e] = __ldg(src + e);
     }
-    float* x0 = c.xb;
-    for (int i = tid; i < D::NBP; i += nthr) x0[i] = i < NX ? tail[D::tXI0 + i] : (i < NB ? tail[D::tUP + i - NX] : 0.0f);
-    float* gcache = a.cache + (size_t)b * a.N * 2 * NX * NX;
+    for (int i = tid; i < NBP; i += nthr)
+        c.xb[i] = i < NX ? __ldg(tail + D::tXI0 + i) : (i < NB ? __ldg(tail + D::tUP + i - NX) : 0.0f);
+    // vectors read as float4 need finite padding
+    for (int e = NBP + tid; e < (a.N + 1) * NBP; e += nthr) c.xb[e] = 0.0f;
+    for (int e = tid; e < a.N * RoundSmem<D>::kTmp * NBP; e += nthr) c.tmp[e] = 0.0f;
+    __syncthreads();
+    auto stage = [&](int k) { return sd + k * D::SREC; };
+    auto mask = [&](int k) { return __float_as_uint(stage(k)[D::oMASK]); };
+    float* gcache = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
     float* gstate = a.state + (size_t)b * RoundState<D>::floats(a.N);
     const int nvar = RoundState<D>::var_floats(a.N);
-    // vectors read as float4 must have finite padding: clear the scratch, xb, ax, bdu areas
-    for (int e = tid; e < a.N * Smem<D>::kTmpVecs * D::NBP; e += nthr) c.tmp[e] = 0.0f;
-    for (int e = D::NBP + tid; e < (a.N + 1) * D::NBP; e += nthr) c.xb[e] = 0.0f;
-    for (int e = tid; e < a.N * D::NBP; e += nthr) { c.ax[e] = 0.0f; c.bdu[e] = 0.0f; }
-    __syncthreads();
     if (a.m0 == 0) {
         bool bad = false, badset = false;
-        for (int e = tid; e < c.Nh * D::SREC; e += nthr) {
-            const int off = e % D::SREC;
-            if (off < D::oMASK && !isfinite(c.sd[e])) bad = true;
-        }
-        for (int i = tid; i < NB; i += nthr) if (!isfinite(x0[i])) bad = true;
-        for (int e = tid; e < c.Nh * D::NC; e += nthr) {
+        for (int e = tid; e < Nh * D::SREC; e += nthr)
+            if (e % D::SREC < D::oMASK && !isfinite(sd[e])) bad = true;
+        for (int i = tid; i < NB; i += nthr) if (!isfinite(c.xb[i])) bad = true;
+        for (int e = tid; e < Nh * D::NC; e += nthr) {
             const int k = e / D::NC, q = e % D::NC;
-            if (((c.mask(k) >> q) & 1u) && (c.stage(k)[D::oMU + q] < 0.0f || c.stage(k)[D::oFM + q] < 0.0f)) badset = true;
+            if (((mask(k) >> q) & 1u) && (stage(k)[D::oMU + q] < 0.0f || stage(k)[D::oFM + q] < 0.0f)) badset = true;
         }
         const bool any_bad = __syncthreads_or(bad);
         const bool any_badset = __syncthreads_or(badset);
         if (any_bad || any_badset) {
-            write_output<D>(c, wa, b, any_bad ? kNonFinite : kBadSet, 0, 0.0f, 0);
-            if (tid == 0) a.done[b] = 1;
+            round_fail<D>(a, b, any_bad ? kNonFinite : kBadSet);
             return;
         }
-        if (warp < c.Nh) {
-            const int j = warp;
-            const float* sj = c.stage(j);
-            float* Sj = c.Sm + j * NX * NX;
-            for (int e = lane; e < NX * NX; e += 32) {
-                const int r = e / NX, cc = e % NX;
-                float acc = (r == cc) ? 1.0f : 0.0f;
-                for (int i = 0; i < NU; ++i) acc = fmaf(sj[D::oB + r * NU + i], sj[D::oB + cc * NU + i], acc);
-                Sj[e] = acc;
-            }
-            __syncwarp();
-            warp_inverse_spd(Sj, NX, lane);
-            if (j >= 1) {
-                const float* sp = c.stage(j - 1);
-                float* Wj = c.Wm + j * NX * NX;
-                for (int e = lane; e < NX * NX; e += 32) {
-                    const int r = e / NX, cc = e % NX;
-                    float acc = (r == cc) ? 1.0f / a.rho : 0.0f;
-                    for (int i = 0; i < NX; ++i)
-                        acc = fmaf(sj[D::oA + r * NX + i] * sj[D::oA + cc * NX + i], 1.0f / (sp[D::oQ + i] + a.rho), acc);
-                    for (int i = 0; i < NU; ++i)
-                        acc = fmaf(sj[D::oB + r * NU + i] * sj[D::oB + cc * NU + i], 1.0f / (sp[D::oR + i] + 2.0f * a.rho), acc);
-                    Wj[e] = acc;
-                }
-                __syncwarp();
-                warp_inverse_spd(Wj, NX, lane);
-            }
-            for (int e = lane; e < NX * NX; e += 32) {
-                gcache[(j * 2 + 0) * NX * NX + e] = Sj[e];
-                if (j >= 1) gcache[(j * 2 + 1) * NX * NX + e] = c.Wm[j * NX * NX + e];
-            }
-        }
-        for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
-        for (int e = tid; e < a.N * D::NC; e += nthr) {
-            a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
-            c.modes[e] = 0u;
-        }
-        if (tid == 0) a.out_npol[b] = 0;
-    } else {
-        for (int e = tid; e < c.Nh * 2 * NX * NX; e += nthr) {
-            const int j = e / (2 * NX * NX), r = e % (2 * NX * NX);
-            (r < NX * NX ? c.Sm + j * NX * NX + r : c.Wm + j * NX * NX + (r - NX * NX))[0] = gcache[e];
-        }
-        const float4* src = reinterpret_cast<const float4*>(gstate);
-        float4* dst = reinterpret_cast<float4*>(c.var);
-        for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
     }
     // per-stage constants: qbar, 1/D' = 1/(Q+rho | R+2rho), 1/D = 1/(Q+rho | R+rho)
-    float* pre = c.hat;  // the hat area is free: extrapolated values are formed where read
-    for (int e = tid; e < c.Nh * D::NBP; e += nthr) {
-        const int k = e / D::NBP, i = e % D::NBP;
-        const float* sk = c.stage(k);
+    for (int e = tid; e < Nh * NBP; e += nthr) {
+        const int k = e / NBP, i = e % NBP;
+        const float* sk = stage(k);
         float qb = 0.0f, idp = 0.0f, idn = 0.0f;
         if (i < NX) {
             qb = sk[D::oQ + i] * sk[D::oRY + i];
@@ -389,100 +456,140 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
             idp = 1.0f / (sk[D::oR + i - NX] + 2.0f * a.rho);
             idn = 1.0f / (sk[D::oR + i - NX] + a.rho);
         }
-        pre[(k * 3 + PQB) * D::NBP + i] = qb;
-        pre[(k * 3 + PID) * D::NBP + i] = idp;
-        pre[(k * 3 + PIDN) * D::NBP + i] = idn;
-    }
-    // Abar_0 xibar_0 (constant)
-    if (warp == 0) {
-        const float* s0 = c.stage(0);
-        if (lane < NX) {
-            float acc = 0.0f;
-            for (int cc = 0; cc < NX; ++cc) acc = fmaf(s0[D::oA + lane * NX + cc], x0[cc], acc);
-            for (int i = 0; i < NU; ++i) acc = fmaf(s0[D::oB + lane * NU + i], x0[NX + i], acc);
-            c.ax[lane] = acc;
-        }
-        for (int i = NX + lane; i < NB; i += 32) c.ax[i] = x0[i];
+        c.pre[(k * 3 + PQB) * NBP + i] = qb;
+        c.pre[(k * 3 + PID) * NBP + i] = idp;
+        c.pre[(k * 3 + PIDN) * NBP + i] = idn;
     }
     __syncthreads();
-    // stage matrices into registers
+    if (a.m0 == 0) {
+        if (warp < Nh) {
+            const int j = warp, r = lane >> 1;
+            float row[NX];
+            auto store = [&](int m) {
+                if (r < NX && !(lane & 1)) {
+                    float* dst = c.fac + ((j * 2 + m) * NX + r) * FR;
+                    float* gdst = gcache + ((j * 2 + m) * NX + r) * FR;
+#pragma unroll
+                    for (int cc = 0; cc < FR; ++cc) {
+                        const float v = cc < NX ? row[cc] : 0.0f;
+                        dst[cc] = v;
+                        gdst[cc] = v;
+                    }
+                }
+            };
+            // S_j = (I + B_j B_j')^{-1}
+            gram_inverse<D>(stage(j), nullptr, 1.0f, NX, lane, row);
+            store(0);
+            // W_j = (I/rho + T_j D'^{-1}_{j-1} T_j')^{-1}
+            if (j >= 1) {
+                gram_inverse<D>(stage(j), c.P(j - 1, PID), 1.0f / a.rho, 0, lane, row);
+                store(1);
+            }
+        }
+        for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
+        for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
+        if (tid == 0) a.out_npol[b] = 0;
+    } else {
+        const float4* fs = reinterpret_cast<const float4*>(gcache);
+        float4* fd = reinterpret_cast<float4*>(c.fac);
+        for (int e = tid; e < Nh * 2 * NX * FR / 4; e += nthr) fd[e] = fs[e];
+        const float4* src = reinterpret_cast<const float4*>(gstate);
+        float4* dst = reinterpret_cast<float4*>(c.var);
+        for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
+    }
+    // stage matrix and per-stage constants into registers
+    const int j = warp < Nh ? warp : 0;
     RegT<D> M;
+    StageRegs<D> R;
     {
-        const int j = warp < c.Nh ? warp : 0;
-        const float* sj = c.stage(j);
+        const float* sj = stage(j);
         auto Tm = [&](int r, int col) { return col < NX ? sj[D::oA + r * NX + col] : sj[D::oB + r * NU + col - NX]; };
         const int r = lane >> 1, h = lane & 1;
 #pragma unroll
         for (int rr = 0; rr < NX; ++rr) {
             M.colA[rr] = (lane < NB) ? Tm(rr, lane) : 0.0f;
-            M.colB[rr] = (32 + lane < NB) ? Tm(rr, 32 + lane) : 0.0f;
+            if constexpr (TWO) M.colB[rr] = (32 + lane < NB) ? Tm(rr, 32 + lane) : 0.0f;
         }
 #pragma unroll
         for (int q = 0; q < D::CS; ++q) {
             const int col = h * D::CS + q;
             M.rowT[q] = (r < NX && col < NB) ? Tm(r, col) : 0.0f;
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int col = h * 8 + q;
-            M.rowS[q] = (r < NX && col < NX) ? c.Sm[j * NX * NX + r * NX + col] : 0.0f;
-            M.rowW[q] = (r < NX && col < NX && j >= 1) ? c.Wm[j * NX * NX + r * NX + col] : 0.0f;
-        }
+        R.e0 = lane < NX ? sj[D::oE + lane] : 0.0f;
+        const int jp = j >= 1 ? j - 1 : 0;
+        R.qbp[0] = lane < NB ? c.P(jp, PQB)[lane] : 0.0f;
+        R.idp[0] = lane < NB ? c.P(jp, PID)[lane] : 0.0f;
+        R.qbp[1] = (TWO && lane < NB - 32) ? c.P(jp, PQB)[32 + lane] : 0.0f;
+        R.idp[1] = (TWO && lane < NB - 32) ? c.P(jp, PID)[32 + lane] : 0.0f;
+        const int q = lane < D::NC ? lane : 0;
+        R.mu = sj[D::oMU + q];
+        R.fmx = sj[D::oFM + q];
+        R.stance = (mask(j) >> q) & 1u;
+        R.mw = 0u;
     }
-    Ctx2<D> c2;
-    c2.var = c.var; c2.xb = c.xb; c2.ax = c.ax; c2.bdu = c.bdu; c2.tmp = c.tmp; c2.pre = pre;
-    c2.sd = c.sd; c2.part = c.part; c2.modes = c.modes;
-    c2.N = a.N; c2.Nh = c.Nh; c2.rho = a.rho; c2.dx = a.dx; c2.dy = a.dy;
-    float alpha = 1.0f, cprev = INFINITY;
-    c2.wgt = 0.0f;
-    c2.restart = false;
-    c2.cb = 0;
+    __syncthreads();
+    // Abar_0 xibar_0 is constant; the other stages form theirs every iteration
+    {
+        const float ar = prod_T<D>(M, c.xb, lane);
+        const float axs = __shfl_sync(0xffffffffu, ar, (2 * lane) & 31);
+        R.ax[0] = lane < NX ? axs : (lane < NB ? c.xb[lane] : 0.0f);
+        R.ax[1] = (TWO && lane < NB - 32) ? c.xb[32 + lane] : 0.0f;
+    }
+    float alpha = 1.0f, cprev = INFINITY, wgt = 0.0f;
+    bool restart = false;
+    int cb = 0;
     if (a.m0 > 0) {
         const float* sc = gstate + nvar;
         alpha = sc[RoundState<D>::sAlpha];
         cprev = sc[RoundState<D>::sCprev];
-        c2.wgt = sc[RoundState<D>::sWgt];
-        c2.restart = sc[RoundState<D>::sRestart] != 0.0f;
-        c2.cb = __float_as_int(sc[RoundState<D>::sCb]);
+        wgt = sc[RoundState<D>::sWgt];
+        restart = sc[RoundState<D>::sRestart] != 0.0f;
+        cb = __float_as_int(sc[RoundState<D>::sCb]);
     }
+    const bool active = warp < Nh;
     for (int m = a.m0 + 1; m <= a.m1; ++m) {
-        if (warp < c.Nh) block1_reg<D>(c2, M, warp, lane);
+        const float wa = restart ? 0.0f : 1.0f + wgt, wb = restart ? 1.0f : -wgt;
+        if (active) {
+            load_hats<D>(c, R, cb, j, lane, wa, wb);
+            block1_r<D>(c, M, R, cb, j, lane, wa, wb);
+        }
         __syncthreads();
-        if (warp < c.Nh) block2_reg<D>(c2, warp, lane);
+        if (active) {
+            const float cm = block2_r<D>(c, R, cb, j, lane, a.dx, a.dy);
+            if (lane == 0) c.part[j] = cm;
+        }
         __syncthreads();
-        float tot = 0.0f;
-        for (int j = 0; j < c.Nh; ++j) tot += c.part[j];
-        tot *= a.rho;
+        float tot = lane < Nh ? c.part[lane] : 0.0f;
+        tot = warp_sum(tot) * a.rho;
         if (a.accel) {
             if (tot < a.eta * cprev) {
                 const float an = 0.5f * (1.0f + sqrtf(1.0f + 4.0f * alpha * alpha));
-                c2.wgt = (alpha - 1.0f) / an;
+                wgt = (alpha - 1.0f) / an;
                 alpha = an;
                 cprev = tot;
-                c2.restart = false;
+                restart = false;
             } else {
                 alpha = 1.0f;
-                c2.wgt = 0.0f;
-                c2.restart = true;
+                wgt = 0.0f;
+                restart = true;
                 cprev = cprev / a.eta;
             }
         }
-        c2.cb = 1 - c2.cb;
+        cb = 1 - cb;
     }
-    __syncthreads();
     {
         const float4* src = reinterpret_cast<const float4*>(c.var);
         float4* dst = reinterpret_cast<float4*>(gstate);
         for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
     }
-    for (int e = tid; e < c.Nh * D::NC; e += nthr) a.modes[(size_t)b * a.N * D::NC + e] = c.modes[e];
+    if (active && lane < D::NC && a.m1 > a.m0) a.modes[((size_t)b * a.N + j) * D::NC + lane] = R.mw;
     if (tid == 0) {
         float* sc = gstate + nvar;
         sc[RoundState<D>::sAlpha] = alpha;
         sc[RoundState<D>::sCprev] = cprev;
-        sc[RoundState<D>::sWgt] = c2.wgt;
-        sc[RoundState<D>::sRestart] = c2.restart ? 1.0f : 0.0f;
-        sc[RoundState<D>::sCb] = __int_as_float(c2.cb);
+        sc[RoundState<D>::sWgt] = wgt;
+        sc[RoundState<D>::sRestart] = restart ? 1.0f : 0.0f;
+        sc[RoundState<D>::sCb] = __int_as_float(cb);
     }
 }
 

@@ -33,6 +33,8 @@ struct Shape {
     cudaError_t (*set_round_attrs)(int round_bytes, int polish_bytes);
     void (*launch_round)(const RoundArgs&, int B, int smem, cudaStream_t);
     void (*launch_polish)(const RoundArgs&, int B, int smem, cudaStream_t);
+    int (*round_smem)(int N);
+    int (*cache_floats)(int N);
 };
 
 template <class D>
@@ -51,6 +53,10 @@ template <class D>
 int polish_smem_t(int N) { return CtaSmem<D>(N).total * 4; }
 template <class D>
 int state_floats_t(int N) { return RoundState<D>::floats(N); }
+template <class D>
+int round_smem_t(int N) { return RoundSmem<D>(N).bytes(); }
+template <class D>
+int cache_floats_t(int N) { return RoundSmem<D>::cache_floats(N); }
 template <class D>
 cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
     cudaError_t e = cudaFuncSetAttribute(round2_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
@@ -73,7 +79,8 @@ template <class D>
 Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
                  launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
-                 set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>};
+                 set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
+                 cache_floats_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -108,7 +115,7 @@ struct mpc_handle {
     float* out_kkt = nullptr;
     unsigned long long* out_bits = nullptr;
     int* out_npol = nullptr;
-    float* cache = nullptr;      // [B_max][N_max][2][nx*nx] S_j, W_j
+    float* cache = nullptr;      // [B_max][N_max][2][nx][16] S_j, W_j (padded rows)
     float* state = nullptr;      // [B_max][state floats] ADMM iterate between rounds
     uint32_t* modes = nullptr;   // [B_max][N_max][nc]
     uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
@@ -226,7 +233,10 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     if (sh.polish_smem(c.N_max) > max_optin_smem(c.device))
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: polish needs %d B shared memory", c.N_max,
                     sh.polish_smem(c.N_max));
-    if ((e = sh.set_round_attrs(smem, sh.polish_smem(c.N_max))) != cudaSuccess)
+    if (sh.round_smem(c.N_max) > max_optin_smem(c.device))
+        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: ADMM rounds need %d B shared memory", c.N_max,
+                    sh.round_smem(c.N_max));
+    if ((e = sh.set_round_attrs(sh.round_smem(c.N_max), sh.polish_smem(c.N_max))) != cudaSuccess)
         return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
 
     mpc_handle* h = new (std::nothrow) mpc_handle();
@@ -240,7 +250,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t rec_b = B * h->irec * sizeof(float);
     const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * h->nu * sizeof(float);
     const size_t small_b = B * (3 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
-    const size_t cache_b = B * N * 2 * c.nx * c.nx * sizeof(float);
+    const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
     const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
@@ -368,7 +378,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.done = h->done; r.active = h->active; r.Kst = h->Kst;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol;
-    const int round_smem = h->shape.smem_bytes(h->N_set);
+    const int round_smem = h->shape.round_smem(h->N_set);
     const int polish_smem = h->shape.polish_smem(h->N_set);
     if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");

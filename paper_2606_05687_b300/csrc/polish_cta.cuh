@@ -1,10 +1,19 @@
 // Polish, certificate and active-set refinement with one 128-thread CTA per
-// instance (4 warps).  The algebra is that of warp_polish / warp_certificate
-// in polish.cuh (backward Riccati scan on the reduced inputs, forward
-// rollout, KKT terms, projected-gradient face update); here the per-stage
-// products are spread over 128 threads with CTA barriers, the 24x24
-// Cholesky factorisation stays in one warp's registers, and the 14
-// right-hand sides of the two triangular solves are split over the 4 warps.
+// instance (4 warps), after each ADMM round.
+//   polish:      the active faces of the latest projection fix some input
+//                components (u = T ut + o); the equality-constrained LQR on
+//                the remaining free components is solved by a backward
+//                Riccati scan (full-size per-stage systems whose eliminated
+//                columns are unit vectors, Gauss-Jordan over the free pivots
+//                only, operands in registers and 64-byte shared rows), then
+//                a forward rollout;
+//   certificate: costate scan, stationarity, per-contact nonnegative
+//                multipliers (cyclic coordinate descent) and the KKT
+//                residual of Sec. IV's stopping test;
+//   refinement:  faces re-read from the projection of u - alpha sigma w, then
+//                polish again (at most refine_steps times).
+// Stage records are staged through shared memory with a register prefetch
+// of the next stage.
 #pragma once
 #include "polish.cuh"
 
@@ -12,29 +21,42 @@ namespace pinmpc {
 
 constexpr int kPT = 128;  // threads per polish CTA
 
+// Approximate reciprocal (PTX rcp.approx, relative error below 2^-22); used
+// for elimination pivots, whose rounding is far below the certificate's tolerance.
+__device__ __forceinline__ float rcp_approx(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 template <class D>
 struct CtaSmem {
-    static constexpr int NX = D::NX, NU = D::NU, NK = NX + 1, W = NU + NK;  // W: columns of [M | RHS]
-    static constexpr int al(int x) { return (x + 3) & ~3; }
-    static constexpr int oP = 0, op = al(oP + NX * NX), oS = al(op + NX), osv = al(oS + NX * NX),
-                         oSA = al(osv + NX), oSB = al(oSA + NX * NX), oSe = al(oSB + NX * NU), oet = al(oSe + NX),
-                         oBt = al(oet + NX), oRt = al(oBt + NX * NU), ogt = al(oRt + NU), oot = al(ogt + NU),
-                         oA0 = al(oot + NU), oA1 = al(oA0 + NU * W), oK = al(oA1 + NU * W),
-                         og2 = al(oK + NU * NK), oidx = al(og2 + NX), opos = al(oidx + NU), onf = al(opos + NU),
-                         out = al(onf + 4),
-                         obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC), ored = al(obuf1 + D::SREC),
-                         oFixed = al(ored + 32);
-    static_assert(oK % 4 == 0 && obuf0 % 4 == 0 && obuf1 % 4 == 0, "16-byte regions for float4 traffic");
+    static constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
+    static constexpr int XP = 16;  // padded row length (NX + 1 <= 16)
+    static_assert(NK <= XP && NU <= 32, "polish layout assumes nx < 16 and nu <= 32");
+    static constexpr int al(int x) { return (x + 15) & ~15; }
+    // backward scan (all 64-byte aligned rows of XP floats):
+    //   Xp = [P | p] of the stage after, S = Q + sym(P), AT = A', BtT = Bt' (reduced map),
+    //   SBT = (S Bt)', SAT = (S A)', K16 = [K | kappa], GR = [G | g2]
+    static constexpr int oXp = 0, oS = al(oXp + NX * XP), oAT = al(oS + XP * XP), oBtT = al(oAT + NX * XP),
+                         oRt = al(oBtT + NU * XP), ogt = al(oRt + 32), oot = al(ogt + 32), oet = al(oot + 32),
+                         osv = al(oet + XP), odv = al(osv + XP), oSBT = al(odv + XP), oSAT = al(oSBT + NU * XP),
+                         oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
+                         oprow = al(opcol + 64), ofree = al(oprow + 2 * 48), oScanEnd = al(ofree + 4),
+                         // forward rollout and certificate
+                         oK = oScanEnd, out = al(oK + NU * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
+                         ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
+    static_assert(NU + NK <= 48, "pivot-row buffer");
     int xr, ur, y, wv, modes, cmu, cfm, cmask, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
         xr = take((N + 1) * NX);
         ur = take(N * NU);
-        // the certificate runs after the scan: costates reuse an elimination
-        // buffer, the gradient the S/SA/SB/Se area, when they fit
-        y = (N * NX <= NU * W) ? oA0 : take(N * NX);
-        wv = (N * NU <= oet - oS) ? oS : take(N * NU);
+        // the certificate runs after the scan: costates and the gradient
+        // reuse scan buffers when they fit
+        y = (N * NX <= (oK16 - oSBT)) ? oSBT : take(N * NX);
+        wv = (N * NU <= (oprow - oK16)) ? oK16 : take(N * NU);
         modes = take(N * D::NC);
         cmu = take(N * D::NC);
         cfm = take(N * D::NC);
@@ -117,32 +139,78 @@ __device__ __forceinline__ void cta_rollout_step(const CCtx<D>& c, const float* 
     }
 }
 
+// dot of the first NX entries of two 16-float rows (64-byte aligned)
+template <int NX>
+__device__ __forceinline__ float dot_row(const float* a, const float* b) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (NX + 3) / 4; ++q) {
+        const float4 u = a4[q], v = b4[q];
+        if (4 * q + 0 < NX) s0 = fmaf(u.x, v.x, s0);
+        if (4 * q + 1 < NX) s1 = fmaf(u.y, v.y, s1);
+        if (4 * q + 2 < NX) s0 = fmaf(u.z, v.z, s0);
+        if (4 * q + 3 < NX) s1 = fmaf(u.w, v.w, s1);
+    }
+    return s0 + s1;
+}
+
+// dot of the first NX entries of a 16-float row with a register vector
+template <int NX>
+__device__ __forceinline__ float dot_reg(const float* a, const float (&v)[NX]) {
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (NX + 3) / 4; ++q) {
+        const float4 u = a4[q];
+        if (4 * q + 0 < NX) s0 = fmaf(u.x, v[4 * q + 0], s0);
+        if (4 * q + 1 < NX) s1 = fmaf(u.y, v[4 * q + 1], s1);
+        if (4 * q + 2 < NX) s0 = fmaf(u.z, v[4 * q + 2], s0);
+        if (4 * q + 3 < NX) s1 = fmaf(u.w, v[4 * q + 3], s1);
+    }
+    return s0 + s1;
+}
+
 // Backward Riccati scan + forward rollout of one instance by one CTA.
+//
+// Stage k of the scan, with (P, p) of stage k+1 (zero after the last stage)
+// and the reduced input map u = T ut + o of the stage's faces (Bt = Bs T,
+// Rt = T'RsT diagonal, gt = T'Rs(o - rus); an eliminated column has Bt = 0,
+// Rt = 1, gt = 0):
+//   S = Q + P, s = Q ry + p, et = e + Bs o,
+//   M = Rt + Bt'S Bt, [K | kappa] = M^{-1} [-Bt'S A | Bt'(s - S et) - gt],
+//   G = S A + S Bt K, g2 = s - S et - S Bt kappa, P = A'G, p = A'g2.
+// M is kept at full size: an eliminated column makes row and column of M a
+// unit vector and its row of the right-hand side zero, so its elimination
+// step is skipped and its gains come out zero.
 template <class D>
 __device__ void cta_polish(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
     using CS = CtaSmem<D>;
+    constexpr int XP = CS::XP;
     const int tid = c.tid;
     float* sm = c.sm;
-    float* P = sm + CS::oP;
-    float* p = sm + CS::op;
+    float* Xp = sm + CS::oXp;
     float* S = sm + CS::oS;
-    float* sv = sm + CS::osv;
-    float* SA = sm + CS::oSA;
-    float* SB = sm + CS::oSB;
-    float* Se = sm + CS::oSe;
-    float* et = sm + CS::oet;
-    float* Bt = sm + CS::oBt;
+    float* AT = sm + CS::oAT;
+    float* BtT = sm + CS::oBtT;
     float* Rt = sm + CS::oRt;
     float* gts = sm + CS::ogt;
     float* ots = sm + CS::oot;
-    float* Aug0 = sm + CS::oA0;
-    float* Aug1 = sm + CS::oA1;
+    float* et = sm + CS::oet;
+    float* sv = sm + CS::osv;
+    float* dv = sm + CS::odv;
+    float* SBT = sm + CS::oSBT;
+    float* SAT = sm + CS::oSAT;
+    float* K16 = sm + CS::oK16;
+    float* GR = sm + CS::oGR;
+    float* pcol = sm + CS::opcol;
+    float* prow = sm + CS::oprow;
+    uint32_t* freep = reinterpret_cast<uint32_t*>(sm + CS::ofree);
     float* Ks = sm + CS::oK;
-    float* g2 = sm + CS::og2;
-    for (int e = tid; e < NX * NX + NX; e += kPT) {
-        if (e < NX * NX) P[e] = 0.0f; else p[e - NX * NX] = 0.0f;
-    }
+    // all scan buffers start at zero: their padding stays zero
+    for (int e = tid; e < CS::oScanEnd; e += kPT) sm[e] = 0.0f;
     CPrefetch<D::SREC, true> pf;
     pf.load(c.grec(c.Nh - 1), tid);
     for (int k = c.Nh - 1; k >= 0; --k) {
@@ -151,165 +219,217 @@ __device__ void cta_polish(const CCtx<D>& c) {
         pf.store(s, tid);
         __syncthreads();
         if (k > 0) pf.load(c.grec(k - 1), tid);
-        // reduced input map, one column per thread; eliminated columns (swing
-        // or apex contacts, face-fixed components) have bt = 0 and rt = 1
-        int* idx = reinterpret_cast<int*>(sm + CS::oidx);  // free columns, compacted
-        int* pos = reinterpret_cast<int*>(sm + CS::opos);  // column -> position in idx, or -1
-        int* nfs = reinterpret_cast<int*>(sm + CS::onf);
+        // (1) warp 0: reduced input map (one column per lane), free columns, et.
+        //     warps 1..3: S = Q + sym(P), s = Q ry + p, AT = A'
         if (tid < 32) {
             bool fr = false;
             if (tid < NU) {
                 float bt[NX], rt, gt, ot;
                 reduced_column<D>(c, s, c.modes[k * D::NC + tid / D::CD], tid, bt, rt, gt, ot);
+                float4* row = reinterpret_cast<float4*>(BtT + tid * XP);
 #pragma unroll
-                for (int r = 0; r < NX; ++r) {
-                    Bt[r * NU + tid] = bt[r];
-                    fr |= (bt[r] != 0.0f);
+                for (int q = 0; q < XP / 4; ++q) {
+                    const int r = 4 * q;
+                    row[q] = make_float4(r < NX ? bt[r] : 0.0f, r + 1 < NX ? bt[r + 1] : 0.0f,
+                                         r + 2 < NX ? bt[r + 2] : 0.0f, r + 3 < NX ? bt[r + 3] : 0.0f);
                 }
+#pragma unroll
+                for (int r = 0; r < NX; ++r) fr |= (bt[r] != 0.0f);
                 fr |= (rt != 1.0f) || (gt != 0.0f);
                 Rt[tid] = rt;
                 gts[tid] = gt;
                 ots[tid] = ot;
             }
             const unsigned ball = __ballot_sync(0xffffffffu, fr);
-            const int a = __popc(ball & ((1u << tid) - 1u));
-            if (tid < NU) {
-                pos[tid] = fr ? a : -1;
-                if (fr) idx[a] = tid;
-            }
-            if (tid == 0) nfs[0] = __popc(ball);
-        }
-        __syncthreads();
-        const int nf = nfs[0];
-        // et = e + Bs ot ; S = diag(Q) + P ; s = Q ry + p
-        for (int e = tid; e < NX * NX + 2 * NX; e += kPT) {
-            if (e < NX * NX) {
-                const int r = e / NX, cc = e % NX;
-                S[e] = P[e] + (r == cc ? s[D::oQ + r] : 0.0f);
-            } else if (e < NX * NX + NX) {
-                const int r = e - NX * NX;
-                float acc = s[D::oE + r];
+            if (tid == 0) freep[0] = ball;
+            __syncwarp();
+            if (tid < NX) {
+                float acc = s[D::oE + tid];
 #pragma unroll
-                for (int i = 0; i < NU; ++i) acc = fmaf(s[D::oB + r * NU + i], ots[i], acc);
-                et[r] = acc;
-            } else {
-                const int r = e - NX * NX - NX;
-                sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], p[r]);
+                for (int i = 0; i < NU; ++i) acc = fmaf(s[D::oB + tid * NU + i], ots[i], acc);
+                et[tid] = acc;
+            }
+        } else {
+            for (int e = tid - 32; e < NX * XP + NX + NX * NX; e += kPT - 32) {
+                if (e < NX * XP) {
+                    const int r = e / XP, cc = e % XP;
+                    S[e] = cc < NX ? 0.5f * (Xp[r * XP + cc] + Xp[cc * XP + r]) + (r == cc ? s[D::oQ + r] : 0.0f) : 0.0f;
+                } else if (e < NX * XP + NX) {
+                    const int r = e - NX * XP;
+                    sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], Xp[r * XP + NX]);
+                } else {
+                    const int f = e - NX * XP - NX, i = f / NX, cc = f % NX;
+                    AT[cc * XP + i] = s[D::oA + f];
+                }
             }
         }
         __syncthreads();
-        // SB = S Bt on the free columns (SB[r][a], a < nf), SA = S A, Se = S et
-        for (int e = tid; e < NX * (nf + NX + 1); e += kPT) {
-            const int r = e / (nf + NX + 1), col = e % (nf + NX + 1);
-            float acc = 0.0f;
-            if (col < nf) {
-                const int ic = idx[col];
-#pragma unroll
-                for (int i = 0; i < NX; ++i) acc = fmaf(S[r * NX + i], Bt[i * NU + ic], acc);
-                SB[r * NU + col] = acc;
-            } else if (col < nf + NX) {
-#pragma unroll
-                for (int i = 0; i < NX; ++i) acc = fmaf(S[r * NX + i], s[D::oA + i * NX + col - nf], acc);
-                SA[r * NX + col - nf] = acc;
-            } else {
-#pragma unroll
-                for (int i = 0; i < NX; ++i) acc = fmaf(S[r * NX + i], et[i], acc);
-                Se[r] = acc;
-            }
-        }
-        __syncthreads();
-        // [M_ff | RHS_f] on the free rows/columns: M = Rt + Bt' S Bt,
-        // RHS = [-Bt' S A | Bt'(s - S et) - gt]
-        const int W = nf + NK;
-        for (int e = tid; e < nf * W; e += kPT) {
-            const int a = e / W, j = e % W, ia = idx[a];
-            float acc;
-            if (j < nf) {
-                acc = (a == j) ? Rt[ia] : 0.0f;
-#pragma unroll
-                for (int r = 0; r < NX; ++r) acc = fmaf(Bt[r * NU + ia], SB[r * NU + j], acc);
-            } else if (j < nf + NX) {
-                acc = 0.0f;
-#pragma unroll
-                for (int r = 0; r < NX; ++r) acc = fmaf(Bt[r * NU + ia], SA[r * NX + j - nf], acc);
-                acc = -acc;
-            } else {
-                acc = -gts[ia];
-#pragma unroll
-                for (int r = 0; r < NX; ++r) acc = fmaf(Bt[r * NU + ia], sv[r] - Se[r], acc);
-            }
-            Aug0[e] = acc;
-        }
-        __syncthreads();
-        // Gauss-Jordan elimination without pivoting (M_ff is SPD): after nf
-        // steps the right block holds X = M_ff^{-1} RHS_f.  Each thread owns one
-        // column and a group of rows; the two buffers alternate so a step
-        // needs one barrier.
+        const uint32_t fmask = freep[0];
+        // (2) SBT = (S Bt)', SAT = (S A)', Se: thread (column, row group) with
+        //     its 16-float column in registers
         {
-            const int G = kPT / W;                 // row groups (>= 3)
-            const int RPG = (nf + G - 1) / G;      // rows per group (<= 8)
-            const int j = tid % W, g = tid / W;
-            const float* X = Aug0;
-            float* Y = Aug1;
-#pragma unroll 1
-            for (int pp = 0; pp < nf; ++pp) {
-                if (g < G && j > pp) {
-                    const float prj = X[pp * W + j] * __frcp_rn(X[pp * W + pp]);
+            constexpr int W2 = NU + NX + 1, G2 = kPT / W2, R2 = (NX + G2 - 1) / G2;
+            const int col = tid % W2, g = tid / W2;
+            if (g < G2) {
+                const float* src = col < NU ? BtT + col * XP : (col < NU + NX ? AT + (col - NU) * XP : et);
+                float v[NX];
 #pragma unroll
-                    for (int t = 0; t < (NU + 2) / 3; ++t) {
-                        const int i = g * RPG + t;
-                        if (t < RPG && i < nf)
-                            Y[i * W + j] = (i == pp) ? prj : fmaf(-X[i * W + pp], prj, X[i * W + j]);
+                for (int i = 0; i < NX; ++i) v[i] = src[i];
+#pragma unroll
+                for (int t = 0; t < R2; ++t) {
+                    const int r = g * R2 + t;
+                    if (r < NX) {
+                        const float acc = dot_reg<NX>(S + r * XP, v);
+                        if (col < NU) SBT[col * XP + r] = acc;
+                        else if (col < NU + NX) SAT[(col - NU) * XP + r] = acc;
+                        else dv[r] = sv[r] - acc;
                     }
                 }
-                __syncthreads();
-                const float* T = X;
-                X = Y;
-                Y = const_cast<float*>(T);
-            }
-            // gains: free rows from the solve, eliminated rows 0
-            float* Kg = c.K + (size_t)k * NU * NK;
-            for (int e = tid; e < NU * NK; e += kPT) {
-                const int a = pos[e / NK];
-                const float v = (a >= 0) ? X[a * W + nf + (e % NK)] : 0.0f;
-                Ks[e] = v;
-                Kg[e] = v;
             }
         }
         __syncthreads();
-        // G = SA + SB K (in place over SA), g2 = s - Se - SB kappa
-        for (int e = tid; e < NX * NX + NX; e += kPT) {
-            if (e < NX * NX) {
-                const int r = e / NX, cc = e % NX;
-                float acc = SA[e];
-                for (int a = 0; a < nf; ++a) acc = fmaf(SB[r * NU + a], Ks[idx[a] * NK + cc], acc);
-                SA[e] = acc;
-            } else {
-                const int r = e - NX * NX;
-                float acc = sv[r] - Se[r];
-                for (int a = 0; a < nf; ++a) acc = fmaf(-SB[r * NU + a], Ks[idx[a] * NK + NX], acc);
-                g2[r] = acc;
-            }
-        }
-        __syncthreads();
-        // P = sym(A' G), p = A' g2
-        for (int e = tid; e < NX * NX + NX; e += kPT) {
-            if (e < NX * NX) {
-                const int r = e / NX, cc = e % NX;
-                float a1 = 0.0f, a2 = 0.0f;
+        // (3) [M | RHS] straight into the registers of the elimination: thread
+        //     (column j, row group g) holds rows g RG .. g RG + RG - 1 of column j
+        constexpr int W = NU + NK, G = kPT / W, RG = (NU + G - 1) / G;
+        const int j = tid % W, g = tid / W;
+        const bool own = g < G;
+        float x[RG];
+        {
+            const float* src = j < NU ? SBT + j * XP : (j < NU + NX ? SAT + (j - NU) * XP : dv);
+            float v[NX];
 #pragma unroll
-                for (int i = 0; i < NX; ++i) {
-                    a1 = fmaf(s[D::oA + i * NX + r], SA[i * NX + cc], a1);
-                    a2 = fmaf(s[D::oA + i * NX + cc], SA[i * NX + r], a2);
-                }
-                P[e] = 0.5f * (a1 + a2);
-            } else {
-                const int r = e - NX * NX;
+            for (int i = 0; i < NX; ++i) v[i] = own ? src[i] : 0.0f;
+#pragma unroll
+            for (int t = 0; t < RG; ++t) {
+                const int a = g * RG + t;
                 float acc = 0.0f;
-#pragma unroll
-                for (int i = 0; i < NX; ++i) acc = fmaf(s[D::oA + i * NX + r], g2[i], acc);
-                p[r] = acc;
+                if (own && a < NU) {
+                    acc = dot_reg<NX>(BtT + a * XP, v);
+                    if (j < NU) acc += (a == j) ? Rt[a] : 0.0f;
+                    else if (j < NU + NX) acc = -acc;
+                    else acc -= gts[a];
+                }
+                x[t] = acc;
             }
+        }
+        // (4) Gauss-Jordan elimination without pivoting (M is SPD) over the
+        //     free columns only.  Before step pp the owners publish the pivot
+        //     column and the pivot row into double-buffered vectors, so a step
+        //     needs one barrier; the row group holding the pivot row then
+        //     overwrites it with the scaled row.  Afterwards the right block
+        //     holds [K | kappa].
+        {
+            auto publish = [&](int pp, int bsel) {
+                if (own && j == pp) {
+#pragma unroll
+                    for (int t = 0; t < RG; ++t) {
+                        const int a = g * RG + t;
+                        if (a < NU) pcol[bsel * 32 + a] = x[t];
+                    }
+                }
+                if (own && g == pp / RG) {
+                    const int tp = pp - g * RG;
+                    float v = x[0];
+#pragma unroll
+                    for (int t = 1; t < RG; ++t) v = (t == tp) ? x[t] : v;
+                    prow[bsel * 48 + j] = v;
+                }
+            };
+            uint32_t rem = fmask;
+            int bsel = 0;
+            if (rem) publish(__ffs(rem) - 1, 0);
+            __syncthreads();
+            while (rem) {
+                const int pp = __ffs(rem) - 1;
+                rem &= rem - 1;
+                if (own && j > pp) {
+                    const float prj = prow[bsel * 48 + j] * rcp_approx(prow[bsel * 48 + pp]);
+                    const float* pc = pcol + bsel * 32 + g * RG;
+#pragma unroll
+                    for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[t], prj, x[t]);
+                    if (g == pp / RG) {
+                        const int tp = pp - g * RG;
+#pragma unroll
+                        for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? prj : x[t];
+                    }
+                }
+                bsel ^= 1;
+                if (rem) publish(__ffs(rem) - 1, bsel);
+                __syncthreads();
+            }
+        }
+        // (5) gains to K16 (scan) and to global memory (rollout)
+        {
+            float* Kg = c.K + (size_t)k * NU * NK;
+            if (own && j >= NU) {
+#pragma unroll
+                for (int t = 0; t < RG; ++t) {
+                    const int a = g * RG + t;
+                    if (a < NU) {
+                        K16[a * XP + (j - NU)] = x[t];
+                        Kg[a * NK + (j - NU)] = x[t];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (6) GR = [G | g2]: G = SA + SB K, g2 = dv - SB kappa; thread (row r,
+        //     column quad cq, half h of the inputs), halves combined by a shuffle
+        {
+            const int h = tid & 1, cq = (tid >> 1) & 3, r = tid >> 3;
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (r < NX) {
+#pragma unroll
+                for (int a = 0; a < NU; a += 2) {
+                    const int aa = a + h;
+                    if (aa < NU && ((fmask >> aa) & 1u)) {
+                        const float sb = SBT[aa * XP + r];
+                        const float4 kv = reinterpret_cast<const float4*>(K16 + aa * XP)[cq];
+                        acc.x = fmaf(sb, kv.x, acc.x);
+                        acc.y = fmaf(sb, kv.y, acc.y);
+                        acc.z = fmaf(sb, kv.z, acc.z);
+                        acc.w = fmaf(sb, kv.w, acc.w);
+                    }
+                }
+            }
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 1);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 1);
+            if (r < NX && h == 0) {
+                float o[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int cc = 4 * cq + q;
+                    o[q] = cc < NX ? SAT[cc * XP + r] + o[q] : (cc == NX ? dv[r] - o[q] : 0.0f);
+                }
+                reinterpret_cast<float4*>(GR + r * XP)[cq] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        __syncthreads();
+        // (7) Xp = A' [G | g2] = [P | p] (symmetrised when the next stage reads it)
+        {
+            const int h = tid & 1, cq = (tid >> 1) & 3, r = tid >> 3;
+            float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (r < NX) {
+#pragma unroll
+                for (int i = 0; i < NX; i += 2) {
+                    const int ii = i + h;
+                    if (ii < NX) {
+                        const float at = AT[r * XP + ii];
+                        const float4 gv = reinterpret_cast<const float4*>(GR + ii * XP)[cq];
+                        acc.x = fmaf(at, gv.x, acc.x);
+                        acc.y = fmaf(at, gv.y, acc.y);
+                        acc.z = fmaf(at, gv.z, acc.z);
+                        acc.w = fmaf(at, gv.w, acc.w);
+                    }
+                }
+            }
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+            acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 1);
+            acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 1);
+            if (r < NX && h == 0) reinterpret_cast<float4*>(Xp + r * XP)[cq] = acc;
         }
     }
     // forward rollout: ut = K x + kappa, u = T ut + o, x' = A x + Bs u + e
@@ -567,7 +687,7 @@ __device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, in
 
 // Polish / certify / refine after a round: one CTA per instance.
 template <class D>
-__global__ void __launch_bounds__(kPT) polish_cta_kernel(RoundArgs a) {
+__global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float psm[];
     constexpr int NX = D::NX, NU = D::NU;
     const int b = blockIdx.x;
@@ -625,7 +745,7 @@ __global__ void __launch_bounds__(kPT) polish_cta_kernel(RoundArgs a) {
         __syncthreads();
         for (int e = c.tid; e < c.Nh * NU; e += kPT) {
             const int k = e / NU, i = e % NU;
-            c.ur()[e] = st[((cb * 5 + VZ) * a.N + k) * D::NBP + NX + i];
+            c.ur()[e] = st[RoundState<D>::at(a.N, cb, k, VZ) + NX + i];
         }
         cta_rollout<D>(c);
         kkt = cta_certificate<D>(c);
