@@ -32,17 +32,20 @@ __device__ __forceinline__ float rcp_approx(float v) {
 template <class D>
 struct CtaSmem {
     static constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
-    static constexpr int XP = 16;  // padded row length (NX + 1 <= 16)
-    static_assert(NK <= XP && NU <= 32, "polish layout assumes nx < 16 and nu <= 32");
+    // padded row length: 16-byte aligned rows (float4), and consecutive rows
+    // start in different bank quads, so lanes reading different rows as
+    // float4 do not conflict
+    static constexpr int XP = 20;
+    static_assert(NK <= 16 && NU <= 32, "polish layout assumes nx < 16 and nu <= 32");
     static constexpr int al(int x) { return (x + 15) & ~15; }
-    // backward scan (all 64-byte aligned rows of XP floats):
+    // backward scan (rows of XP floats):
     //   Xp = [P | p] of the stage after, S = Q + sym(P), AT = A', BtT = Bt' (reduced map),
     //   SBT = (S Bt)', SAT = (S A)', K16 = [K | kappa], GR = [G | g2]
     static constexpr int oXp = 0, oS = al(oXp + NX * XP), oAT = al(oS + XP * XP), oBtT = al(oAT + NX * XP),
                          oRt = al(oBtT + NU * XP), ogt = al(oRt + 32), oot = al(ogt + 32), oet = al(oot + 32),
                          osv = al(oet + XP), odv = al(osv + XP), oSBT = al(odv + XP), oSAT = al(oSBT + NU * XP),
                          oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
-                         oprow = al(opcol + 64), ofree = al(oprow + 2 * 48), oScanEnd = al(ofree + 4),
+                         oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oScanEnd = al(ofree + 4),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + NU * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
                          ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
@@ -139,26 +142,23 @@ __device__ __forceinline__ void cta_rollout_step(const CCtx<D>& c, const float* 
     }
 }
 
-// dot of the first NX entries of two 16-float rows (64-byte aligned)
+// first 4 ceil(NX/4) entries of a 16-byte aligned row into registers
 template <int NX>
-__device__ __forceinline__ float dot_row(const float* a, const float* b) {
-    const float4* a4 = reinterpret_cast<const float4*>(a);
-    const float4* b4 = reinterpret_cast<const float4*>(b);
-    float s0 = 0.0f, s1 = 0.0f;
+__device__ __forceinline__ void load_row(const float* src, float (&v)[4 * ((NX + 3) / 4)]) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
     for (int q = 0; q < (NX + 3) / 4; ++q) {
-        const float4 u = a4[q], v = b4[q];
-        if (4 * q + 0 < NX) s0 = fmaf(u.x, v.x, s0);
-        if (4 * q + 1 < NX) s1 = fmaf(u.y, v.y, s1);
-        if (4 * q + 2 < NX) s0 = fmaf(u.z, v.z, s0);
-        if (4 * q + 3 < NX) s1 = fmaf(u.w, v.w, s1);
+        const float4 t = s4[q];
+        v[4 * q + 0] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
     }
-    return s0 + s1;
 }
 
-// dot of the first NX entries of a 16-float row with a register vector
+// dot of the first NX entries of a 16-byte aligned row with a register vector
 template <int NX>
-__device__ __forceinline__ float dot_reg(const float* a, const float (&v)[NX]) {
+__device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((NX + 3) / 4)]) {
     const float4* a4 = reinterpret_cast<const float4*>(a);
     float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
@@ -272,9 +272,8 @@ __device__ void cta_polish(const CCtx<D>& c) {
             const int col = tid % W2, g = tid / W2;
             if (g < G2) {
                 const float* src = col < NU ? BtT + col * XP : (col < NU + NX ? AT + (col - NU) * XP : et);
-                float v[NX];
-#pragma unroll
-                for (int i = 0; i < NX; ++i) v[i] = src[i];
+                float v[4 * ((NX + 3) / 4)];
+                load_row<NX>(src, v);
 #pragma unroll
                 for (int t = 0; t < R2; ++t) {
                     const int r = g * R2 + t;
@@ -296,9 +295,8 @@ __device__ void cta_polish(const CCtx<D>& c) {
         float x[RG];
         {
             const float* src = j < NU ? SBT + j * XP : (j < NU + NX ? SAT + (j - NU) * XP : dv);
-            float v[NX];
-#pragma unroll
-            for (int i = 0; i < NX; ++i) v[i] = own ? src[i] : 0.0f;
+            float v[4 * ((NX + 3) / 4)];
+            load_row<NX>(src, v);
 #pragma unroll
             for (int t = 0; t < RG; ++t) {
                 const int a = g * RG + t;
@@ -313,48 +311,95 @@ __device__ void cta_polish(const CCtx<D>& c) {
             }
         }
         // (4) Gauss-Jordan elimination without pivoting (M is SPD) over the
-        //     free columns only.  Before step pp the owners publish the pivot
-        //     column and the pivot row into double-buffered vectors, so a step
-        //     needs one barrier; the row group holding the pivot row then
-        //     overwrites it with the scaled row.  Afterwards the right block
-        //     holds [K | kappa].
+        //     free columns only, two pivots (p1 < p2) per step: the owners
+        //     publish both pivot columns and both pivot rows of the current
+        //     matrix into double-buffered vectors (one barrier per step), and
+        //     each column j takes
+        //       r1 = X[p1][j] / d1,  d2 = X[p2][p2] - X[p2][p1] X[p1][p2] / d1,
+        //       y2 = (X[p2][j] - X[p2][p1] r1) / d2,  y1 = r1 - X[p1][p2] y2 / d1,
+        //       X[a][j] -= X[a][p1] y1 + X[a][p2] y2,  rows p1, p2 <- y1, y2
+        //     (two successive single-pivot steps written out).  Afterwards
+        //     the right block holds [K | kappa].
         {
-            auto publish = [&](int pp, int bsel) {
-                if (own && j == pp) {
+            auto publish = [&](int p1, int p2, int bsel) {
+                float* pc = pcol + bsel * 64;
+                float* pr = prow + bsel * 96;
+                if (own && (j == p1 || j == p2)) {
+                    float* dst = pc + (j == p1 ? 0 : 32);
 #pragma unroll
                     for (int t = 0; t < RG; ++t) {
                         const int a = g * RG + t;
-                        if (a < NU) pcol[bsel * 32 + a] = x[t];
+                        if (a < NU) dst[a] = x[t];
                     }
                 }
-                if (own && g == pp / RG) {
-                    const int tp = pp - g * RG;
-                    float v = x[0];
 #pragma unroll
-                    for (int t = 1; t < RG; ++t) v = (t == tp) ? x[t] : v;
-                    prow[bsel * 48 + j] = v;
+                for (int w = 0; w < 2; ++w) {
+                    const int pp = w == 0 ? p1 : p2;
+                    if (pp >= 0 && own && g == pp / RG) {
+                        const int tp = pp - g * RG;
+                        float v = x[0];
+#pragma unroll
+                        for (int t = 1; t < RG; ++t) v = (t == tp) ? x[t] : v;
+                        pr[w * 48 + j] = v;
+                    }
                 }
+            };
+            auto pair_of = [](uint32_t m, int& p1, int& p2) {
+                p1 = __ffs(m) - 1;
+                m &= m - 1;
+                p2 = m ? __ffs(m) - 1 : -1;
             };
             uint32_t rem = fmask;
             int bsel = 0;
-            if (rem) publish(__ffs(rem) - 1, 0);
+            if (rem) {
+                int p1, p2;
+                pair_of(rem, p1, p2);
+                publish(p1, p2, 0);
+            }
             __syncthreads();
             while (rem) {
-                const int pp = __ffs(rem) - 1;
+                int q1, q2;
+                pair_of(rem, q1, q2);
                 rem &= rem - 1;
-                if (own && j > pp) {
-                    const float prj = prow[bsel * 48 + j] * rcp_approx(prow[bsel * 48 + pp]);
-                    const float* pc = pcol + bsel * 32 + g * RG;
+                if (q2 >= 0) rem &= rem - 1;
+                if (own && j > q1) {
+                    const float* pc = pcol + bsel * 64 + g * RG;
+                    const float* pr = prow + bsel * 96;
+                    const float d1i = rcp_approx(pr[q1]);
+                    const float r1 = pr[j] * d1i;
+                    if (q2 >= 0) {
+                        const float a12 = pr[q2] * d1i;
+                        const float d2 = fmaf(-pr[48 + q1], a12, pr[48 + q2]);
+                        const float y2 = fmaf(-pr[48 + q1], r1, pr[48 + j]) * rcp_approx(d2);
+                        const float y1 = fmaf(-a12, y2, r1);
 #pragma unroll
-                    for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[t], prj, x[t]);
-                    if (g == pp / RG) {
-                        const int tp = pp - g * RG;
+                        for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[32 + t], y2, fmaf(-pc[t], y1, x[t]));
+                        if (g == q1 / RG) {
+                            const int tp = q1 - g * RG;
 #pragma unroll
-                        for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? prj : x[t];
+                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? y1 : x[t];
+                        }
+                        if (g == q2 / RG) {
+                            const int tp = q2 - g * RG;
+#pragma unroll
+                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? y2 : x[t];
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[t], r1, x[t]);
+                        if (g == q1 / RG) {
+                            const int tp = q1 - g * RG;
+#pragma unroll
+                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? r1 : x[t];
+                        }
                     }
                 }
                 bsel ^= 1;
-                if (rem) publish(__ffs(rem) - 1, bsel);
+                if (rem) {
+                    int p1, p2;
+                    pair_of(rem, p1, p2);
+                    publish(p1, p2, bsel);
+                }
                 __syncthreads();
             }
         }
