@@ -105,6 +105,43 @@ __device__ __forceinline__ float2 prod_Tt(const RegT<D>& M, const float* x) {
     return make_float2(a0, a1);
 }
 
+// Exact projection onto the point-contact pyramid {|t_x|, |t_y| <= mu n,
+// 0 <= n <= nmax}: project_contact for contact_dim 3, where both cone
+// coefficients equal mu.  The candidate pieces of phi are then the empty set,
+// the larger tangential component and both, n = (a_n + mu sum_S |a_j|) /
+// (1 + |S| mu^2), so with ir1 = 1/(1 + mu^2) and ir2 = 1/(1 + 2 mu^2)
+// precomputed there is no division.  Any extra feasible candidate cannot
+// beat the unique minimiser of the strictly convex phi.
+__device__ __forceinline__ uint32_t project_point(const float* a, float* out, float mu, float nmax, float ir1,
+                                                  float ir2) {
+    const float ax = a[0], ay = a[1], an = a[2];
+    const float tx = fabsf(ax), ty = fabsf(ay);
+    const float n0 = fminf(fmaxf(an, 0.0f), nmax);
+    const float n1 = fminf(fmaxf(fmaf(mu, fmaxf(tx, ty), an) * ir1, 0.0f), nmax);
+    const float n2 = fminf(fmaxf(fmaf(mu, tx + ty, an) * ir2, 0.0f), nmax);
+    auto phi = [&](float n) {
+        const float dn = n - an, ex = fmaxf(fmaf(-mu, n, tx), 0.0f), ey = fmaxf(fmaf(-mu, n, ty), 0.0f);
+        return fmaf(dn, dn, fmaf(ex, ex, ey * ey));
+    };
+    float n = n0, best = phi(n0);
+    const float p1 = phi(n1), p2 = phi(n2);
+    if (p1 < best) { best = p1; n = n1; }
+    if (p2 < best) n = n2;
+    uint32_t mode = 0;
+    if (n <= 0.0f) mode |= 1u << 4;
+    if (n >= nmax) mode |= 1u << 5;
+    const float lim = mu * n;
+    float t0 = ax, t1 = ay;
+    if (ax >= lim) { t0 = lim; mode |= 1u << 0; }
+    if (ax <= -lim) { t0 = -lim; mode |= 1u << 1; }
+    if (ay >= lim) { t1 = lim; mode |= 1u << 2; }
+    if (ay <= -lim) { t1 = -lim; mode |= 1u << 3; }
+    out[0] = t0;
+    out[1] = t1;
+    out[2] = n;
+    return mode;
+}
+
 // per-stage constant vectors kept in shared memory: qbar, 1/D' (k < N-1 form), 1/D (last stage form)
 enum : int { PQB = 0, PID = 1, PIDN = 2 };
 
@@ -128,6 +165,7 @@ struct StageRegs {
     float e0;                 // ebar_j[lane] (0 beyond NX)
     float qbp[2], idp[2];     // qbar_{j-1} and 1/D'_{j-1}
     float mu, fmx;            // contact lane q: friction coefficient and force bound
+    float ir1, ir2;           // contact lane q: 1/(1 + mu^2), 1/(1 + 2 mu^2) (point contacts)
     uint32_t stance;          // contact lane q is in stance
     uint32_t mw;              // contact lane q: faces of the latest projection
     float ax[2];              // Abar_j xibar_j
@@ -284,7 +322,10 @@ __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int
     if (lane < D::NC) {
         const int q = lane;
         if (R.stance) {
-            R.mw = project_contact<CD>(arg + NX + q * CD, zp + NX + q * CD, R.mu, R.fmx, dx, dy);
+            if constexpr (CD == 3)
+                R.mw = project_point(arg + NX + q * CD, zp + NX + q * CD, R.mu, R.fmx, R.ir1, R.ir2);
+            else
+                R.mw = project_contact<CD>(arg + NX + q * CD, zp + NX + q * CD, R.mu, R.fmx, dx, dy);
         } else {
 #pragma unroll
             for (int i = 0; i < CD; ++i) zp[NX + q * CD + i] = 0.0f;
@@ -524,6 +565,8 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
         const int q = lane < D::NC ? lane : 0;
         R.mu = sj[D::oMU + q];
         R.fmx = sj[D::oFM + q];
+        R.ir1 = 1.0f / (1.0f + R.mu * R.mu);
+        R.ir2 = 1.0f / (1.0f + 2.0f * R.mu * R.mu);
         R.stance = (mask(j) >> q) & 1u;
         R.mw = 0u;
     }
