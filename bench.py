@@ -317,10 +317,11 @@ def run_gpu(args):
     if rank != 0:
         return
     # kernels per step: pack + (round + polish) per round; rounds end once every instance is done
-    rounds, m1, interval = 1, 20, 10.0
+    cfg = solver.cfg
+    rounds, m1, interval = 1, min(cfg.check_start, cfg.max_iter), float(cfg.check_every)
     while m1 < int(iters.max()):
-        m1 = int(min(m1 + interval, args.max_iter))
-        interval *= 2.0
+        m1 = int(min(m1 + interval, cfg.max_iter))
+        interval *= cfg.check_growth
         rounds += 1
     flops = float(flops_per_solve(iters.astype(np.float64), polishes.astype(np.float64), N).sum())
     solve_avg = statistics.mean(solve_ms)

@@ -171,14 +171,14 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->u_scale = 300.0f;
     cfg->max_iter = 1000;
     cfg->kkt_tol = 5e-6f;
-    cfg->check_start = 20;
-    cfg->check_every = 10;
+    cfg->check_start = 12;
+    cfg->check_every = 20;
     cfg->check_growth = 2.0f;
     cfg->polish = 1;
     cfg->accel = 1;
     cfg->restart_eta = 0.999f;
     cfg->refine_steps = 3;
-    cfg->refine_alpha = 0.05f;
+    cfg->refine_alpha = 0.01f;
     cfg->foot_half_length = 0.10f;
     cfg->foot_half_width = 0.05f;
     cfg->mem_budget = 0;
