@@ -411,6 +411,82 @@ __device__ __forceinline__ void gram_inverse(const float* sj, const float* d, fl
     }
 }
 
+// Per-stage factors of the ADMM round, one warp per (instance, stage):
+// S_j = (I + B_j B_j')^{-1} and W_j = (I/rho + T_j D'^{-1}_{j-1} T_j')^{-1},
+// written to the factor cache as 16-float padded rows, and the input checks
+// of the stage (non-finite data; a stance contact with negative friction
+// coefficient or force bound) as per-instance flag bits (1, 2).  Runs at
+// full occupancy ahead of the first round, which then only loads the cache.
+struct FactorArgs {
+    const float* rec;
+    int irec, n_rec, N, B;
+    float rho;
+    float* cache;  // [B][N][2][NX][16]
+    int* flags;    // [B], zeroed before the launch
+};
+constexpr int kFactorWarps = 8;
+
+template <class D>
+__global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a) {
+    constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
+    static_assert(D::SREC % 4 == 0, "records are copied as float4");
+    __shared__ __align__(16) float s_rec[kFactorWarps][D::SREC];
+    __shared__ __align__(16) float s_d[kFactorWarps][NBP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kFactorWarps + warp;
+    if (gw >= a.B * a.N) return;  // whole warps leave; the kernel has no CTA barrier
+    const int b = gw / a.N, j = gw % a.N;
+    const float* rec = a.rec + (size_t)b * a.irec;
+    const float* tail = rec + (size_t)a.n_rec * D::SREC;
+    const int Nh0 = __float_as_int(__ldg(tail + D::tH));
+    const int Nh = (Nh0 >= 1 && Nh0 <= a.N) ? Nh0 : 0;
+    if (j >= Nh) return;
+    float* sr = s_rec[warp];
+    float* dd = s_d[warp];
+    {
+        const float4* src = reinterpret_cast<const float4*>(rec + (size_t)j * D::SREC);
+        for (int e = lane; e < D::SREC / 4; e += 32) reinterpret_cast<float4*>(sr)[e] = __ldg(src + e);
+    }
+    if (j >= 1) {
+        const float* sp = rec + (size_t)(j - 1) * D::SREC;
+        for (int i = lane; i < NBP; i += 32)
+            dd[i] = i < NX ? 1.0f / (__ldg(sp + D::oQ + i) + a.rho)
+                           : (i < NB ? 1.0f / (__ldg(sp + D::oR + i - NX) + 2.0f * a.rho) : 0.0f);
+    }
+    __syncwarp();
+    bool bad = false, badset = false;
+    for (int e = lane; e < D::oMASK; e += 32) bad |= !isfinite(sr[e]);
+    if (j == 0) {
+        for (int i = lane; i < NB; i += 32)
+            bad |= !isfinite(__ldg(tail + (i < NX ? D::tXI0 + i : D::tUP + i - NX)));
+    }
+    const uint32_t mk = __float_as_uint(sr[D::oMASK]);
+    if (lane < D::NC && ((mk >> lane) & 1u)) badset = sr[D::oMU + lane] < 0.0f || sr[D::oFM + lane] < 0.0f;
+    bad = __any_sync(0xffffffffu, bad);
+    badset = __any_sync(0xffffffffu, badset);
+    if (lane == 0 && (bad || badset)) atomicOr(a.flags + b, (bad ? 1 : 0) | (badset ? 2 : 0));
+    float* gc = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
+    const int r = lane >> 1;
+    float row[NX];
+    auto store = [&](int m) {
+        if (r < NX && !(lane & 1)) {
+            float4* dst = reinterpret_cast<float4*>(gc + ((j * 2 + m) * NX + r) * FR);
+#pragma unroll
+            for (int q = 0; q < FR / 4; ++q) {
+                const int c0 = 4 * q;
+                dst[q] = make_float4(c0 < NX ? row[c0] : 0.0f, c0 + 1 < NX ? row[c0 + 1] : 0.0f,
+                                     c0 + 2 < NX ? row[c0 + 2] : 0.0f, c0 + 3 < NX ? row[c0 + 3] : 0.0f);
+            }
+        }
+    };
+    gram_inverse<D>(sr, nullptr, 1.0f, NX, lane, row);
+    store(0);
+    if (j >= 1) {
+        gram_inverse<D>(sr, dd, 1.0f / a.rho, 0, lane, row);
+        store(1);
+    }
+}
+
 // Writes a failure status for instance b (no iterate): zero trajectory and inputs.
 template <class D>
 __device__ void round_fail(const RoundArgs& a, int b, int status) {
@@ -446,6 +522,13 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
         round_fail<D>(a, b, kBadHorizon);
         return;
     }
+    if (a.m0 == 0) {
+        const int fl = a.flags[b];  // written by factor_kernel
+        if (fl) {
+            round_fail<D>(a, b, (fl & 1) ? kNonFinite : kBadSet);
+            return;
+        }
+    }
     RCtx<D> c;
     c.var = smem + L.var; c.xb = smem + L.xb; c.tmp = smem + L.tmp; c.pre = smem + L.pre;
     c.fac = smem + L.fac; c.part = smem + L.part;
@@ -468,22 +551,6 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     float* gcache = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
     float* gstate = a.state + (size_t)b * RoundState<D>::floats(a.N);
     const int nvar = RoundState<D>::var_floats(a.N);
-    if (a.m0 == 0) {
-        bool bad = false, badset = false;
-        for (int e = tid; e < Nh * D::SREC; e += nthr)
-            if (e % D::SREC < D::oMASK && !isfinite(sd[e])) bad = true;
-        for (int i = tid; i < NB; i += nthr) if (!isfinite(c.xb[i])) bad = true;
-        for (int e = tid; e < Nh * D::NC; e += nthr) {
-            const int k = e / D::NC, q = e % D::NC;
-            if (((mask(k) >> q) & 1u) && (stage(k)[D::oMU + q] < 0.0f || stage(k)[D::oFM + q] < 0.0f)) badset = true;
-        }
-        const bool any_bad = __syncthreads_or(bad);
-        const bool any_badset = __syncthreads_or(badset);
-        if (any_bad || any_badset) {
-            round_fail<D>(a, b, any_bad ? kNonFinite : kBadSet);
-            return;
-        }
-    }
     // per-stage constants: qbar, 1/D' = 1/(Q+rho | R+2rho), 1/D = 1/(Q+rho | R+rho)
     for (int e = tid; e < Nh * NBP; e += nthr) {
         const int k = e / NBP, i = e % NBP;
@@ -502,38 +569,16 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
         c.pre[(k * 3 + PIDN) * NBP + i] = idn;
     }
     __syncthreads();
+    {
+        const float4* fs = reinterpret_cast<const float4*>(gcache);
+        float4* fd = reinterpret_cast<float4*>(c.fac);
+        for (int e = tid; e < Nh * 2 * NX * FR / 4; e += nthr) fd[e] = fs[e];
+    }
     if (a.m0 == 0) {
-        if (warp < Nh) {
-            const int j = warp, r = lane >> 1;
-            float row[NX];
-            auto store = [&](int m) {
-                if (r < NX && !(lane & 1)) {
-                    float* dst = c.fac + ((j * 2 + m) * NX + r) * FR;
-                    float* gdst = gcache + ((j * 2 + m) * NX + r) * FR;
-#pragma unroll
-                    for (int cc = 0; cc < FR; ++cc) {
-                        const float v = cc < NX ? row[cc] : 0.0f;
-                        dst[cc] = v;
-                        gdst[cc] = v;
-                    }
-                }
-            };
-            // S_j = (I + B_j B_j')^{-1}
-            gram_inverse<D>(stage(j), nullptr, 1.0f, NX, lane, row);
-            store(0);
-            // W_j = (I/rho + T_j D'^{-1}_{j-1} T_j')^{-1}
-            if (j >= 1) {
-                gram_inverse<D>(stage(j), c.P(j - 1, PID), 1.0f / a.rho, 0, lane, row);
-                store(1);
-            }
-        }
         for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
         for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
         if (tid == 0) a.out_npol[b] = 0;
     } else {
-        const float4* fs = reinterpret_cast<const float4*>(gcache);
-        float4* fd = reinterpret_cast<float4*>(c.fac);
-        for (int e = tid; e < Nh * 2 * NX * FR / 4; e += nthr) fd[e] = fs[e];
         const float4* src = reinterpret_cast<const float4*>(gstate);
         float4* dst = reinterpret_cast<float4*>(c.var);
         for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];

@@ -35,6 +35,7 @@ struct Shape {
     void (*launch_polish)(const RoundArgs&, int B, int smem, cudaStream_t);
     int (*round_smem)(int N);
     int (*cache_floats)(int N);
+    void (*launch_factor)(const FactorArgs&, cudaStream_t);
 };
 
 template <class D>
@@ -58,6 +59,11 @@ int round_smem_t(int N) { return RoundSmem<D>(N).bytes(); }
 template <class D>
 int cache_floats_t(int N) { return RoundSmem<D>::cache_floats(N); }
 template <class D>
+void launch_factor_t(const FactorArgs& a, cudaStream_t s) {
+    const int warps = a.B * a.N;
+    factor_kernel<D><<<(warps + kFactorWarps - 1) / kFactorWarps, 32 * kFactorWarps, 0, s>>>(a);
+}
+template <class D>
 cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
     cudaError_t e = cudaFuncSetAttribute(round2_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
@@ -80,7 +86,7 @@ Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
                  launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
-                 cache_floats_t<D>};
+                 cache_floats_t<D>, launch_factor_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -120,6 +126,7 @@ struct mpc_handle {
     uint32_t* modes = nullptr;   // [B_max][N_max][nc]
     uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
     int* done = nullptr;         // [B_max]
+    int* flags = nullptr;        // [B_max] input-check bits of the factor kernel
     int* active = nullptr;       // running-instance counter
     int* active_host = nullptr;  // pinned host copy of the counter
     float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
@@ -254,7 +261,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
     const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
-    const size_t round_b = cache_b + state_b + 2 * modes_b + B * sizeof(int) + sizeof(int) + kst_b;
+    const size_t round_b = cache_b + state_b + 2 * modes_b + 2 * B * sizeof(int) + sizeof(int) + kst_b;
     h->bytes = rec_b + xi_b + u_b + small_b + round_b;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }
@@ -274,6 +281,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->cache, cache_b) == cudaSuccess && cudaMalloc(&h->state, state_b) == cudaSuccess &&
               cudaMalloc(&h->modes, modes_b) == cudaSuccess && cudaMalloc(&h->lastm, modes_b) == cudaSuccess &&
               cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->flags, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->active, sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess &&
               cudaMallocHost(&h->active_host, sizeof(int)) == cudaSuccess;
     if (!ok) {
@@ -375,13 +383,23 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
     r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
     r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
-    r.done = h->done; r.active = h->active; r.Kst = h->Kst;
+    r.done = h->done; r.active = h->active; r.Kst = h->Kst; r.flags = h->flags;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol;
     const int round_smem = h->shape.round_smem(h->N_set);
     const int polish_smem = h->shape.polish_smem(h->N_set);
     if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");
+    if ((e = cudaMemsetAsync(h->flags, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMemsetAsync");
+    // per-stage factors and input checks for the whole batch
+    {
+        FactorArgs fa{};
+        fa.rec = h->rec; fa.irec = h->irec; fa.n_rec = c.N_max; fa.N = h->N_set; fa.B = B;
+        fa.rho = c.rho; fa.cache = h->cache; fa.flags = h->flags;
+        h->shape.launch_factor(fa, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "factor kernel launch");
+    }
     // rounds of ADMM iterations, each followed by the polish/certify kernel;
     // stop once no instance is running (host reads the counter each round)
     int m0 = 0;
@@ -468,6 +486,7 @@ void mpc_destroy(mpc_handle* h) {
     cudaFree(h->modes);
     cudaFree(h->lastm);
     cudaFree(h->done);
+    cudaFree(h->flags);
     cudaFree(h->active);
     cudaFree(h->Kst);
     cudaFreeHost(h->active_host);

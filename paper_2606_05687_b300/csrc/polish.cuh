@@ -26,6 +26,7 @@ struct RoundArgs {
     float refine_alpha;
     int m0, m1;              // this round runs iterations m0+1 .. m1
     float* cache;            // [B][N][2][NX][16]  S_j, W_j (padded rows)
+    const int* flags;        // [B] input-check bits of factor_kernel
     float* state;            // [B][RoundState::floats(N)]
     uint32_t* modes;         // [B][N][NC] faces of the latest z
     uint32_t* lastm;         // [B][N][NC] faces of the last polished z

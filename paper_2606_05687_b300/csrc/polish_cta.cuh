@@ -45,11 +45,17 @@ struct CtaSmem {
                          oRt = al(oBtT + NU * XP), ogt = al(oRt + 32), oot = al(ogt + 32), oet = al(oot + 32),
                          osv = al(oet + XP), odv = al(osv + XP), oSBT = al(odv + XP), oSAT = al(oSBT + NU * XP),
                          oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
-                         oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oScanEnd = al(ofree + 4),
+                         oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oMC = al(ofree + 4),
+                         opcb = al(oMC + (NU + NK) * 32), oScanEnd = al(opcb + 2 * 32),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + NU * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
                          ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
     static_assert(NU + NK <= 48, "pivot-row buffer");
+    // column stride of the column-major [M | RHS]: a multiple of 4 at least NU
+    // with an odd number of float4s, so consecutive columns read as float4
+    // fall in different bank quads
+    static constexpr int CP = (((NU + 3) / 4) % 2 == 1) ? 4 * ((NU + 3) / 4) : 4 * ((NU + 3) / 4) + 4;
+    static_assert(CP <= 32, "column buffer");
     int xr, ur, y, wv, modes, cmu, cfm, cmask, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
@@ -205,8 +211,6 @@ __device__ void cta_polish(const CCtx<D>& c) {
     float* SAT = sm + CS::oSAT;
     float* K16 = sm + CS::oK16;
     float* GR = sm + CS::oGR;
-    float* pcol = sm + CS::opcol;
-    float* prow = sm + CS::oprow;
     uint32_t* freep = reinterpret_cast<uint32_t*>(sm + CS::ofree);
     float* Ks = sm + CS::oK;
     // all scan buffers start at zero: their padding stays zero
@@ -287,133 +291,106 @@ __device__ void cta_polish(const CCtx<D>& c) {
             }
         }
         __syncthreads();
-        // (3) [M | RHS] straight into the registers of the elimination: thread
-        //     (column j, row group g) holds rows g RG .. g RG + RG - 1 of column j
-        constexpr int W = NU + NK, G = kPT / W, RG = (NU + G - 1) / G;
-        const int j = tid % W, g = tid / W;
-        const bool own = g < G;
-        float x[RG];
+        // (3) [M | RHS] column-major into MC: thread (column j, row group g)
+        //     forms rows g RG .. g RG + RG - 1 of column j
+        constexpr int W = NU + NK, CP = CS::CP;
+        float* MC = sm + CS::oMC;
         {
-            const float* src = j < NU ? SBT + j * XP : (j < NU + NX ? SAT + (j - NU) * XP : dv);
-            float v[4 * ((NX + 3) / 4)];
-            load_row<NX>(src, v);
-#pragma unroll
-            for (int t = 0; t < RG; ++t) {
-                const int a = g * RG + t;
-                float acc = 0.0f;
-                if (own && a < NU) {
-                    acc = dot_reg<NX>(BtT + a * XP, v);
-                    if (j < NU) acc += (a == j) ? Rt[a] : 0.0f;
-                    else if (j < NU + NX) acc = -acc;
-                    else acc -= gts[a];
-                }
-                x[t] = acc;
-            }
-        }
-        // (4) Gauss-Jordan elimination without pivoting (M is SPD) over the
-        //     free columns only, two pivots (p1 < p2) per step: the owners
-        //     publish both pivot columns and both pivot rows of the current
-        //     matrix into double-buffered vectors (one barrier per step), and
-        //     each column j takes
-        //       r1 = X[p1][j] / d1,  d2 = X[p2][p2] - X[p2][p1] X[p1][p2] / d1,
-        //       y2 = (X[p2][j] - X[p2][p1] r1) / d2,  y1 = r1 - X[p1][p2] y2 / d1,
-        //       X[a][j] -= X[a][p1] y1 + X[a][p2] y2,  rows p1, p2 <- y1, y2
-        //     (two successive single-pivot steps written out).  Afterwards
-        //     the right block holds [K | kappa].
-        {
-            auto publish = [&](int p1, int p2, int bsel) {
-                float* pc = pcol + bsel * 64;
-                float* pr = prow + bsel * 96;
-                if (own && (j == p1 || j == p2)) {
-                    float* dst = pc + (j == p1 ? 0 : 32);
-#pragma unroll
-                    for (int t = 0; t < RG; ++t) {
-                        const int a = g * RG + t;
-                        if (a < NU) dst[a] = x[t];
-                    }
-                }
-#pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const int pp = w == 0 ? p1 : p2;
-                    if (pp >= 0 && own && g == pp / RG) {
-                        const int tp = pp - g * RG;
-                        float v = x[0];
-#pragma unroll
-                        for (int t = 1; t < RG; ++t) v = (t == tp) ? x[t] : v;
-                        pr[w * 48 + j] = v;
-                    }
-                }
-            };
-            auto pair_of = [](uint32_t m, int& p1, int& p2) {
-                p1 = __ffs(m) - 1;
-                m &= m - 1;
-                p2 = m ? __ffs(m) - 1 : -1;
-            };
-            uint32_t rem = fmask;
-            int bsel = 0;
-            if (rem) {
-                int p1, p2;
-                pair_of(rem, p1, p2);
-                publish(p1, p2, 0);
-            }
-            __syncthreads();
-            while (rem) {
-                int q1, q2;
-                pair_of(rem, q1, q2);
-                rem &= rem - 1;
-                if (q2 >= 0) rem &= rem - 1;
-                if (own && j > q1) {
-                    const float* pc = pcol + bsel * 64 + g * RG;
-                    const float* pr = prow + bsel * 96;
-                    const float d1i = rcp_approx(pr[q1]);
-                    const float r1 = pr[j] * d1i;
-                    if (q2 >= 0) {
-                        const float a12 = pr[q2] * d1i;
-                        const float d2 = fmaf(-pr[48 + q1], a12, pr[48 + q2]);
-                        const float y2 = fmaf(-pr[48 + q1], r1, pr[48 + j]) * rcp_approx(d2);
-                        const float y1 = fmaf(-a12, y2, r1);
-#pragma unroll
-                        for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[32 + t], y2, fmaf(-pc[t], y1, x[t]));
-                        if (g == q1 / RG) {
-                            const int tp = q1 - g * RG;
-#pragma unroll
-                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? y1 : x[t];
-                        }
-                        if (g == q2 / RG) {
-                            const int tp = q2 - g * RG;
-#pragma unroll
-                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? y2 : x[t];
-                        }
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < RG; ++t) x[t] = fmaf(-pc[t], r1, x[t]);
-                        if (g == q1 / RG) {
-                            const int tp = q1 - g * RG;
-#pragma unroll
-                            for (int t = 0; t < RG; ++t) x[t] = (t == tp) ? r1 : x[t];
-                        }
-                    }
-                }
-                bsel ^= 1;
-                if (rem) {
-                    int p1, p2;
-                    pair_of(rem, p1, p2);
-                    publish(p1, p2, bsel);
-                }
-                __syncthreads();
-            }
-        }
-        // (5) gains to K16 (scan) and to global memory (rollout)
-        {
-            float* Kg = c.K + (size_t)k * NU * NK;
-            if (own && j >= NU) {
+            constexpr int G = kPT / W, RG = (NU + G - 1) / G;
+            const int j = tid % W, g = tid / W;
+            if (g < G) {
+                const float* src = j < NU ? SBT + j * XP : (j < NU + NX ? SAT + (j - NU) * XP : dv);
+                float v[4 * ((NX + 3) / 4)];
+                load_row<NX>(src, v);
+                float m[RG];
 #pragma unroll
                 for (int t = 0; t < RG; ++t) {
                     const int a = g * RG + t;
+                    float acc = 0.0f;
                     if (a < NU) {
-                        K16[a * XP + (j - NU)] = x[t];
-                        Kg[a * NK + (j - NU)] = x[t];
+                        acc = dot_reg<NX>(BtT + a * XP, v);
+                        if (j < NU) acc += (a == j) ? Rt[a] : 0.0f;
+                        else if (j < NU + NX) acc = -acc;
+                        else acc -= gts[a];
                     }
+                    m[t] = acc;
+                }
+                if constexpr (RG % 4 == 0 && (NU % RG) == 0) {
+#pragma unroll
+                    for (int q = 0; q < RG / 4; ++q)
+                        reinterpret_cast<float4*>(MC + j * CP + g * RG)[q] =
+                            make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < RG; ++t)
+                        if (g * RG + t < NU) MC[j * CP + g * RG + t] = m[t];
+                }
+            }
+        }
+        __syncthreads();
+        // (4) Gauss-Jordan elimination without pivoting (M is SPD) over the
+        //     free columns only, by two warps (warps 0-1 or 2-3 by CTA parity,
+        //     so co-resident CTAs spread this phase over the SM's schedulers),
+        //     thread j holding all NU entries of column j in registers.  Step pp (fully
+        //     unrolled, so every register index is fixed; skipped uniformly
+        //     when column pp is eliminated): the owner of column pp publishes
+        //     it into a double-buffered vector, then every column takes
+        //     prj = X[pp][j] / X[pp][pp], X[a][j] -= X[a][pp] prj, X[pp][j] = prj
+        //     (column pp itself becomes the unit vector).  Afterwards column
+        //     NU + c holds column c of [K | kappa]; eliminated rows stay zero.
+        const int gj = tid - ((blockIdx.x & 1) ? 64 : 0);  // column index in the eliminating warps
+        if (gj >= 0 && gj < 64) {
+            static_assert(W <= 64, "elimination runs on two warps");
+            float* pcb = sm + CS::opcb;
+            const bool act = gj < W;
+            float xc[4 * (CP / 4)];
+            {
+                const float4* c4 = reinterpret_cast<const float4*>(MC + (act ? gj : 0) * CP);
+#pragma unroll
+                for (int q = 0; q < CP / 4; ++q) {
+                    const float4 t4 = c4[q];
+                    xc[4 * q + 0] = t4.x;
+                    xc[4 * q + 1] = t4.y;
+                    xc[4 * q + 2] = t4.z;
+                    xc[4 * q + 3] = t4.w;
+                }
+            }
+            int bsel = 0;
+#pragma unroll
+            for (int pp = 0; pp < NU; ++pp) {
+                if ((fmask >> pp) & 1u) {
+                    float* buf = pcb + bsel * 32;
+                    if (gj == pp) {
+#pragma unroll
+                        for (int q = 0; q < CP / 4; ++q)
+                            reinterpret_cast<float4*>(buf)[q] =
+                                make_float4(xc[4 * q], xc[4 * q + 1], xc[4 * q + 2], xc[4 * q + 3]);
+                    }
+                    asm volatile("bar.sync 1, 64;" ::: "memory");
+                    float pc[4 * (CP / 4)];
+#pragma unroll
+                    for (int q = 0; q < CP / 4; ++q) {
+                        const float4 t4 = reinterpret_cast<const float4*>(buf)[q];
+                        pc[4 * q + 0] = t4.x;
+                        pc[4 * q + 1] = t4.y;
+                        pc[4 * q + 2] = t4.z;
+                        pc[4 * q + 3] = t4.w;
+                    }
+                    const float prj = xc[pp] * rcp_approx(pc[pp]);
+#pragma unroll
+                    for (int a = 0; a < NU; ++a) xc[a] = fmaf(-pc[a], prj, xc[a]);
+                    xc[pp] = prj;
+                    bsel ^= 1;
+                }
+            }
+            // (5) gains to K16 (scan) and to global memory (rollout)
+            if (act && gj >= NU) {
+                float* Kg = c.K + (size_t)k * NU * NK;
+                const int cc = gj - NU;
+#pragma unroll
+                for (int a = 0; a < NU; ++a) {
+                    K16[a * XP + cc] = xc[a];
+                    Kg[a * NK + cc] = xc[a];
                 }
             }
         }
