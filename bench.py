@@ -6,8 +6,9 @@ mpc_set_stages (pack/scale) + mpc_solve_batch (caches, ADMM, polish,
 certificate, outputs) + mpc_get_traj, inputs resident in HBM.  Only solves
 whose KKT certificate is <= 1e-5 count.  `e2e` repeats the step through the
 same C ABI from pinned host buffers with the host<->device copies inside the
-timed region.  `--impl reference` times the FP64 CPU oracle on a bounded
-sample of the same workload.
+timed region, on two handles and two streams so that the copy of batch k+1
+overlaps the solve of batch k.  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload.
 
 Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
          (N > 1 under torch.distributed.run: weak scaling, one batch per rank)
@@ -33,8 +34,9 @@ B_BENCH, N_BENCH, SEED = 4096, 20, 1002
 KKT_TOL = 1e-5
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# dram bytes per solve-kernel launch from an ncu capture, keyed by the source hash it was taken on
-MEASURED_TRAFFIC = {"ed3c3a110f1ed4ba": 206814208}
+# dram bytes (read + write) per launch of a kernel class from one ncu capture,
+# keyed "class:source hash"; a changed source makes the entry stale (null)
+MEASURED_TRAFFIC = {}
 
 
 def kernel_source_hash() -> str:
@@ -46,21 +48,34 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def flops_per_solve(iters, polishes, N, nx=13, nu=24, nc=8):
-    """Algorithmic FP32 flops of one solve in the implemented (factored) form.
+def kernel_flops(iters, polishes, pivots, horizon, nx=13, nu=24):
+    """Algorithmic FP32 flops (FMA = 2) of one solve of the batch, per kernel class.
 
-    Per stage and ADMM iteration: 6 products with B (nx*nu), 3 with A (nx^2),
-    one each with S_k and W_k (nx^2) -- FMA = 2 flops -- plus ~15 vector
-    flops per lifted component and ~40 per contact projection.  Per polish
-    and stage: the Riccati step (S A, S Bt, Bt'S Bt, Bt'S A, Cholesky, nx+1
-    solves, S Bt K, A'G) and the rollout.  Setup: S_k, W_k formation and
-    inversion."""
-    nb = nx + nu
-    f_it = 2 * (6 * nx * nu + 5 * nx * nx) + 15 * nb + 40 * nc
-    f_ric = 2 * (nx * nx * nx + nx * nx * nu + nu * nu * nx + nu * nx * nx + nu ** 3 / 6
-                 + (nx + 1) * nu * nu + nx * nu * nx + nx * nx * nx) + 2 * (nx * nx + nx * nu)
-    f_setup = 2 * (nx * nx * nu + nx * nx * nb) + 2 * 2 * nx ** 3
-    return N * (iters * f_it + polishes * f_ric + f_setup)
+    round:  the ADMM stage-iteration figure of the hot-path measurement
+            contract, F_it = 2 nu nbar + 2 nbar^2 + 4 (nx^2 + nx nu) + 2 nx nu
+            + 50 nbar (8.9 k at nx 13, nu 24), times stages x iterations.
+    factor: per stage S_j (B B' and a 13x13 inversion, 2 n^3) and, after the
+            first stage, W_j (T D^-1 T' and its inversion).
+    polish: per Riccati scan stage, the full-size stage products as
+            implemented -- S [Bt | A | et], [M | RHS] = Bt'[S Bt | -S A | s - S et],
+            G = S A + S Bt K, A'[G | g2] -- the rollout and the certificate's
+            costate and gradient products; per free pivot actually eliminated,
+            one Gauss-Jordan update of the nu x (nu + nx + 1) system."""
+    nb, nk = nx + nu, nx + 1
+    f_it = 2 * nu * nb + 2 * nb * nb + 4 * (nx * nx + nx * nu) + 2 * nx * nu + 50 * nb
+    f_fac_s = 2 * nx * nx * nu + 2 * nx ** 3
+    f_fac_w = 2 * nx * nx * nb + 2 * nx ** 3
+    f_stage = (2 * nx * nx * (nu + nx + 1) + 2 * nu * nx * (nu + nk) + 2 * nx * nu * nk + 2 * nx * nx * nk
+               + 2 * (nu * nk + nx * nx + nx * nu))
+    f_cert = 2 * nx * nx + 2 * nx * nu
+    f_piv = 2 * nu * (nu + nk)
+    h = np.asarray(horizon, dtype=np.float64)
+    return {
+        "factor": float(np.sum(h * f_fac_s + np.maximum(h - 1, 0) * f_fac_w)),
+        "round": float(np.sum(np.asarray(iters, np.float64) * h) * f_it),
+        "polish": float(np.sum(np.asarray(polishes, np.float64) * h) * (f_stage + f_cert)
+                        + np.sum(np.asarray(pivots, np.float64)) * f_piv),
+    }
 
 
 class Clocks:
@@ -262,6 +277,10 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step()
     barrier()
+    # per-kernel device times of the timed steps: event pairs the library
+    # records around each of its launches on `stream`
+    solver.kernel_times(reset=True)
+    solver.set_kernel_timing(True)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
@@ -272,6 +291,8 @@ def run_gpu(args):
         e_end.record(stream)
         barrier()
     total_ms = e_start.elapsed_time(e_end)
+    ktimes = solver.kernel_times(reset=True)
+    solver.set_kernel_timing(False)
     solve_ms = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
     pack_ms = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
     if world > 1:
@@ -280,52 +301,74 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     ms_per_step = total_ms / args.steps
+    npiv = torch.empty(B, dtype=torch.int32, device=dev)
     solver.get_stats(npol, stream=stream)
+    solver.get_pivots(npiv, stream=stream)
     torch.cuda.synchronize(dev)
     polishes = npol.cpu().numpy()
+    pivots = npiv.cpu().numpy()
     status = st.cpu().numpy()
     iters = it.cpu().numpy()
     kkt = kk.cpu().numpy()
     ok = int(((status == 0) & (kkt <= KKT_TOL)).sum())
     value = world * ok / (ms_per_step / 1e3)
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers.  Two handles on
+    # two streams, as a serving loop would run them: the host-to-device copy
+    # (and packing) of batch k+1 is enqueued before the solve of batch k, so
+    # it overlaps that solve.  Every step still copies all of its inputs in
+    # and its results out inside the timed region.
     h_in = pinmpc.device_inputs(batch, pin_host=True)
-    h_xi = torch.empty((B, N, 13), dtype=torch.float32).pin_memory()
-    h_u = torch.empty((B, N, 24), dtype=torch.float32).pin_memory()
-    h_st = torch.empty(B, dtype=torch.int32).pin_memory()
-    h_kk = torch.empty(B, dtype=torch.float32).pin_memory()
+    solvers = [solver, pinmpc.solver_for(batch, max_iter=args.max_iter)]
+    streams = [stream, torch.cuda.Stream(dev)]
+
+    def pinned_outputs():
+        return (torch.empty((B, N, 13), dtype=torch.float32).pin_memory(),
+                torch.empty((B, N, 24), dtype=torch.float32).pin_memory(),
+                torch.empty(B, dtype=torch.int32).pin_memory(),
+                torch.empty(B, dtype=torch.float32).pin_memory())
+
+    outs = [pinned_outputs(), pinned_outputs()]
     h2d = sum(v.numel() * v.element_size() for v in h_in.values())
-    d2h = sum(v.numel() * v.element_size() for v in (h_xi, h_u, h_st, h_kk))
+    d2h = sum(v.numel() * v.element_size() for v in outs[0])
 
-    def e2e_step():
-        solver.set_stages(B, N, **h_in, stream=stream)
-        solver.solve(B, stream=stream)
-        solver.get_traj(h_xi, h_u, h_st, None, h_kk, None, stream=stream)
+    def e2e_run(K):
+        solvers[0].set_stages(B, N, **h_in, stream=streams[0])
+        for k in range(K):
+            if k + 1 < K:
+                solvers[(k + 1) % 2].set_stages(B, N, **h_in, stream=streams[(k + 1) % 2])
+            sl = k % 2
+            solvers[sl].solve(B, stream=streams[sl])
+            o = outs[sl]
+            solvers[sl].get_traj(o[0], o[1], o[2], None, o[3], None, stream=streams[sl])
+        for sx in streams:
+            sx.synchronize()
 
-    for _ in range(args.warmup):
-        e2e_step()
+    e2e_run(args.warmup)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
+    e2e_run(args.steps)
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_ok = int(((h_st.numpy() == 0) & (h_kk.numpy() <= KKT_TOL)).sum())
+    last = outs[(args.steps - 1) % 2]
+    e2e_ok = int(((last[2].numpy() == 0) & (last[3].numpy() <= KKT_TOL)).sum())
     e2e_val = world * e2e_ok / e2e_s
 
     if rank != 0:
         return
-    # kernels per step: pack + (round + polish) per round; rounds end once every instance is done
-    cfg = solver.cfg
-    rounds, m1, interval = 1, min(cfg.check_start, cfg.max_iter), float(cfg.check_every)
-    while m1 < int(iters.max()):
-        m1 = int(min(m1 + interval, cfg.max_iter))
-        interval *= cfg.check_growth
-        rounds += 1
-    flops = float(flops_per_solve(iters.astype(np.float64), polishes.astype(np.float64), N).sum())
+    # roofline of the dominant kernel from the live per-kernel times (each
+    # timed step solves the same batch, so its work is the last step's times steps)
+    fl = kernel_flops(iters, polishes, pivots, batch.horizon)
+    kt_total = sum(ms for ms, _ in ktimes.values())
+    kernels = {}
+    for name, (ms, n) in ktimes.items():
+        if n == 0:
+            continue
+        tfl = fl.get(name, 0.0) * args.steps / (ms / 1e3) / 1e12 if name in fl else None
+        kernels[name] = {"launches": n, "ms_per_launch": ms / n, "share": ms / kt_total, "achieved_tflops": tfl}
+    dom = max((k for k in kernels if k in fl), key=lambda k: ktimes[k][0])
+    achieved = kernels[dom]["achieved_tflops"]
     solve_avg = statistics.mean(solve_ms)
-    achieved = flops / (solve_avg / 1e3) / 1e12
     h = kernel_source_hash()
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -335,16 +378,18 @@ def run_gpu(args):
                    "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
                    "max_iter": args.max_iter},
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (1 + 2 * rounds),
+        "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(h),
-                     "kernel": "round_kernel + polish_kernel (mpc_solve_batch)", "kernel_ms": solve_avg, "pack_ms": statistics.mean(pack_ms),
-                     "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived)", "src": h},
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
+                     "kernel": dom, "ms_per_launch": kernels[dom]["ms_per_launch"],
+                     "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived; no FP32 peak is measured)",
+                     "kernels": kernels, "solve_ms": solve_avg, "pack_ms": statistics.mean(pack_ms), "src": h},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "solve_stats": {"converged": ok, "iters_mean": float(iters.mean()),
                         "iters_p99": float(np.percentile(iters, 99)), "iters_max": int(iters.max()),
-                        "kkt_max": float(kkt.max()), "polishes_mean": float(polishes.mean())},
+                        "kkt_max": float(kkt.max()), "polishes_mean": float(polishes.mean()),
+                        "free_pivots_mean": float(pivots.mean())},
     }
     print(json.dumps(line), flush=True)
 

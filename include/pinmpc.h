@@ -165,6 +165,26 @@ mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status,
  * or host pointer; host pointers synchronize `stream`. */
 mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream);
 
+/* Free pivots the polish eliminated in the last solve, per instance [B]:
+ * summed over its Riccati scans, the number of free input components of
+ * every stage (the elimination steps actually run).  A work count for
+ * throughput accounting; no counterpart in the paper.  Device or host
+ * pointer; host pointers synchronize `stream`. */
+mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream);
+
+/* Per-kernel device timing (no counterpart in the paper; off by default).
+ * While enabled, mpc_set_stages and mpc_solve_batch record a CUDA event pair
+ * around every kernel they launch, on the caller's stream.
+ * mpc_get_kernel_times waits for the recorded events, adds their durations to
+ * per-class totals and copies the totals out: ms[c] milliseconds and
+ * launches[c] launches of class c = 0 pack, 1 factor, 2 ADMM round,
+ * 3 polish (host arrays of MPC_KERNEL_CLASSES entries; either may be NULL);
+ * reset != 0 clears the totals afterwards.  Events are created on first use
+ * and reused; failure to create one leaves that launch untimed. */
+#define MPC_KERNEL_CLASSES 4
+mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable);
+mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, int32_t reset);
+
 /* Solve a batch without allocating any device memory (no counterpart in the
  * paper; this is a deployment aid).  For callers that may not allocate: code
  * inside someone else's captured CUDA graph, a simulator step that owns a

@@ -499,6 +499,7 @@ __device__ void round_fail(const RoundArgs& a, int b, int status) {
         a.out_iters[b] = 0;
         a.out_kkt[b] = INFINITY;
         a.out_npol[b] = 0;
+        a.out_piv[b] = 0;
         a.done[b] = 1;
     }
 }
@@ -577,7 +578,10 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     if (a.m0 == 0) {
         for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
         for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
-        if (tid == 0) a.out_npol[b] = 0;
+        if (tid == 0) {
+            a.out_npol[b] = 0;
+            a.out_piv[b] = 0;
+        }
     } else {
         const float4* src = reinterpret_cast<const float4*>(gstate);
         float4* dst = reinterpret_cast<float4*>(c.var);

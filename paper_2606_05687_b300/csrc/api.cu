@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/pinmpc.h"
 #include "admm.cuh"
@@ -121,6 +122,7 @@ struct mpc_handle {
     float* out_kkt = nullptr;
     unsigned long long* out_bits = nullptr;
     int* out_npol = nullptr;
+    int* out_piv = nullptr;      // [B_max] free pivots eliminated by the polish
     float* cache = nullptr;      // [B_max][N_max][2][nx][16] S_j, W_j (padded rows)
     float* state = nullptr;      // [B_max][state floats] ADMM iterate between rounds
     uint32_t* modes = nullptr;   // [B_max][N_max][nc]
@@ -136,8 +138,86 @@ struct mpc_handle {
     int B_set = 0, N_set = 0;
     bool have_stages = false, have_solution = false;
     int B_solved = 0;
+    // per-kernel timing (mpc_set_kernel_timing): event pairs recorded around
+    // launches, resolved into totals by mpc_get_kernel_times
+    struct TimedLaunch {
+        int cls;
+        cudaEvent_t start, stop;
+    };
+    bool timing = false;
+    std::vector<cudaEvent_t> event_pool;
+    std::vector<TimedLaunch> pending;
+    double kernel_ms[MPC_KERNEL_CLASSES] = {};
+    int64_t kernel_launches[MPC_KERNEL_CLASSES] = {};
     std::string err;
 };
+
+namespace {
+
+enum : int { kClassPack = 0, kClassFactor = 1, kClassRound = 2, kClassPolish = 3 };
+
+// Waits for the recorded launches, adds their durations to the totals and
+// returns their events to the pool.
+void resolve_timed(mpc_handle* h) {
+    for (const auto& t : h->pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(t.stop) == cudaSuccess && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess) {
+            h->kernel_ms[t.cls] += ms;
+            h->kernel_launches[t.cls] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        h->event_pool.push_back(t.start);
+        h->event_pool.push_back(t.stop);
+    }
+    h->pending.clear();
+}
+
+bool take_event(mpc_handle* h, cudaEvent_t* ev) {
+    if (!h->event_pool.empty()) {
+        *ev = h->event_pool.back();
+        h->event_pool.pop_back();
+        return true;
+    }
+    if (cudaEventCreate(ev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Launches through `launch` on stream s, bracketed by an event pair when timing is on.
+template <class F>
+cudaError_t timed_launch(mpc_handle* h, int cls, cudaStream_t s, F&& launch) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool timed = h->timing;
+    if (timed && h->pending.size() >= 4096) resolve_timed(h);
+    if (timed && !take_event(h, &a)) timed = false;
+    if (timed && !take_event(h, &b)) {
+        h->event_pool.push_back(a);
+        timed = false;
+    }
+    if (timed && cudaEventRecord(a, s) != cudaSuccess) {
+        cudaGetLastError();
+        h->event_pool.push_back(a);
+        h->event_pool.push_back(b);
+        timed = false;
+    }
+    launch();
+    const cudaError_t e = cudaGetLastError();
+    if (timed) {
+        if (cudaEventRecord(b, s) == cudaSuccess) {
+            h->pending.push_back({cls, a, b});
+        } else {
+            cudaGetLastError();
+            h->event_pool.push_back(a);
+            h->event_pool.push_back(b);
+        }
+    }
+    return e;
+}
+
+}  // namespace
 
 static mpc_status fail(mpc_handle* h, mpc_status st, const char* fmt, ...) {
     char buf[512];
@@ -256,7 +336,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t B = (size_t)c.B_max, N = (size_t)c.N_max;
     const size_t rec_b = B * h->irec * sizeof(float);
     const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * h->nu * sizeof(float);
-    const size_t small_b = B * (3 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
+    const size_t small_b = B * (4 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
     const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
@@ -278,6 +358,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->out_kkt, B * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&h->out_bits, B * N * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&h->out_npol, B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->out_piv, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->cache, cache_b) == cudaSuccess && cudaMalloc(&h->state, state_b) == cudaSuccess &&
               cudaMalloc(&h->modes, modes_b) == cudaSuccess && cudaMalloc(&h->lastm, modes_b) == cudaSuccess &&
               cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
@@ -359,8 +440,8 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     a.irec = h->irec;
     a.sigma = c.u_scale;
     a.rec = h->rec;
-    h->shape.launch_pack(a, (int)B, s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "pack kernel launch");
+    if ((e = timed_launch(h, kClassPack, s, [&] { h->shape.launch_pack(a, (int)B, s); })) != cudaSuccess)
+        return cuda_fail(h, e, "pack kernel launch");
     h->B_set = (int)B;
     h->N_set = (int)N;
     h->have_stages = true;
@@ -385,7 +466,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
     r.done = h->done; r.active = h->active; r.Kst = h->Kst; r.flags = h->flags;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
-    r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol;
+    r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
     const int round_smem = h->shape.round_smem(h->N_set);
     const int polish_smem = h->shape.polish_smem(h->N_set);
     if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
@@ -397,8 +478,8 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         FactorArgs fa{};
         fa.rec = h->rec; fa.irec = h->irec; fa.n_rec = c.N_max; fa.N = h->N_set; fa.B = B;
         fa.rho = c.rho; fa.cache = h->cache; fa.flags = h->flags;
-        h->shape.launch_factor(fa, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "factor kernel launch");
+        if ((e = timed_launch(h, kClassFactor, st, [&] { h->shape.launch_factor(fa, st); })) != cudaSuccess)
+            return cuda_fail(h, e, "factor kernel launch");
     }
     // rounds of ADMM iterations, each followed by the polish/certify kernel;
     // stop once no instance is running (host reads the counter each round)
@@ -414,11 +495,11 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         }
         r.m0 = m0;
         r.m1 = m1;
-        h->shape.launch_round(r, B, round_smem, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "round kernel launch");
+        if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_round(r, B, round_smem, st); })) != cudaSuccess)
+            return cuda_fail(h, e, "round kernel launch");
         if ((e = cudaMemsetAsync(h->active, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-        h->shape.launch_polish(r, B, polish_smem, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "polish kernel launch");
+        if ((e = timed_launch(h, kClassPolish, st, [&] { h->shape.launch_polish(r, B, polish_smem, st); })) != cudaSuccess)
+            return cuda_fail(h, e, "polish kernel launch");
         if (m1 >= c.max_iter) break;
         if ((e = cudaMemcpyAsync(h->active_host, h->active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemcpyAsync (counter)");
@@ -469,10 +550,53 @@ mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream) {
     return MPC_OK;
 }
 
+mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_solution) return fail(h, MPC_ERR_STATE, "mpc_get_pivots before mpc_solve_batch");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (pivots) {
+        if ((e = cudaMemcpyAsync(pivots, h->out_piv, (size_t)h->B_solved * 4, cudaMemcpyDefault, s)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMemcpyAsync (pivots)");
+        if (is_host_pointer(pivots) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+    return MPC_OK;
+}
+
+mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return MPC_OK;
+}
+
+mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, int32_t reset) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    resolve_timed(h);
+    for (int i = 0; i < MPC_KERNEL_CLASSES; ++i) {
+        if (ms) ms[i] = h->kernel_ms[i];
+        if (launches) launches[i] = h->kernel_launches[i];
+        if (reset) {
+            h->kernel_ms[i] = 0.0;
+            h->kernel_launches[i] = 0;
+        }
+    }
+    return MPC_OK;
+}
+
 void mpc_destroy(mpc_handle* h) {
     if (!h) return;
     cudaSetDevice(h->cfg.device);
     cudaDeviceSynchronize();
+    for (const auto& t : h->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
+    cudaFree(h->out_piv);
     cudaFree(h->rec);
     cudaFree(h->out_xi);
     cudaFree(h->out_u);

@@ -40,6 +40,7 @@ struct RoundArgs {
     float* out_kkt;
     unsigned long long* out_bits;
     int* out_npol;
+    int* out_piv;            // [B] free pivots eliminated by the polish
 };
 
 // Column i of the reduced input map of one stage (lane i < NU), from the

@@ -178,7 +178,8 @@ __device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((
     return s0 + s1;
 }
 
-// Backward Riccati scan + forward rollout of one instance by one CTA.
+// Backward Riccati scan + forward rollout of one instance by one CTA;
+// returns the number of free pivots eliminated (in every thread).
 //
 // Stage k of the scan, with (P, p) of stage k+1 (zero after the last stage)
 // and the reduced input map u = T ut + o of the stage's faces (Bt = Bs T,
@@ -191,7 +192,7 @@ __device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((
 // unit vector and its row of the right-hand side zero, so its elimination
 // step is skipped and its gains come out zero.
 template <class D>
-__device__ void cta_polish(const CCtx<D>& c) {
+__device__ int cta_polish(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
     using CS = CtaSmem<D>;
     constexpr int XP = CS::XP;
@@ -213,6 +214,7 @@ __device__ void cta_polish(const CCtx<D>& c) {
     float* GR = sm + CS::oGR;
     uint32_t* freep = reinterpret_cast<uint32_t*>(sm + CS::ofree);
     float* Ks = sm + CS::oK;
+    int npiv = 0;
     // all scan buffers start at zero: their padding stays zero
     for (int e = tid; e < CS::oScanEnd; e += kPT) sm[e] = 0.0f;
     CPrefetch<D::SREC, true> pf;
@@ -269,6 +271,7 @@ __device__ void cta_polish(const CCtx<D>& c) {
         }
         __syncthreads();
         const uint32_t fmask = freep[0];
+        npiv += __popc(fmask);
         // (2) SBT = (S Bt)', SAT = (S A)', Se: thread (column, row group) with
         //     its 16-float column in registers
         {
@@ -502,6 +505,7 @@ __device__ void cta_polish(const CCtx<D>& c) {
         cta_rollout_step<D>(c, s, k);
     }
     __syncthreads();
+    return npiv;
 }
 
 // Forward rollout of given (scaled) inputs ur.
@@ -743,18 +747,20 @@ __global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(Rou
     for (int i = c.tid; i < NX; i += kPT) c.xr()[i] = __ldg(tail + D::tXI0 + i);
     changed = __syncthreads_or(changed);
     int npol = a.out_npol[b];
+    int npiv = a.out_piv[b];
     float kkt = INFINITY;
     if (a.polish && changed) {
         for (int e = c.tid; e < c.Nh * D::NC; e += kPT) glast[e] = c.modes[e];
-        cta_polish<D>(c);
+        npiv += cta_polish<D>(c);
         ++npol;
         kkt = cta_certificate<D>(c);
         for (int r = 0; kkt > a.kkt_tol && r < a.refine_steps; ++r) {
             if (!cta_refine_modes<D>(c, a.refine_alpha)) break;
-            cta_polish<D>(c);
+            npiv += cta_polish<D>(c);
             ++npol;
             kkt = cta_certificate<D>(c);
         }
+        if (c.tid == 0) a.out_piv[b] = npiv;
         if (kkt <= a.kkt_tol) {
             cta_write_output<D>(c, a, b, kConverged, a.m1, kkt, npol);
             return;

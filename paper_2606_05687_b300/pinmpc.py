@@ -43,6 +43,9 @@ class StageView(ctypes.Structure):
                 ("mask", _P), ("xi0", _P), ("u_prev", _P), ("horizon", _P)]
 
 
+KERNEL_CLASSES = 4
+KERNEL_CLASS_NAMES = ("pack", "factor", "round", "polish")
+
 _lib = None
 
 
@@ -68,6 +71,13 @@ def load() -> ctypes.CDLL:
     lib.mpc_get_traj.restype = ctypes.c_int
     lib.mpc_get_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mpc_get_stats.restype = ctypes.c_int
+    lib.mpc_get_pivots.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mpc_get_pivots.restype = ctypes.c_int
+    lib.mpc_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.mpc_set_kernel_timing.restype = ctypes.c_int
+    lib.mpc_get_kernel_times.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]
+    lib.mpc_get_kernel_times.restype = ctypes.c_int
     lib.mpc_solve_noalloc.argtypes = [ctypes.POINTER(MpcConfig), ctypes.POINTER(StageView)] + [ctypes.c_void_p] * 6
     lib.mpc_solve_noalloc.restype = ctypes.c_int
     lib.mpc_noalloc_last_error.argtypes = []
@@ -163,6 +173,20 @@ class Solver:
         self._check(self.lib.mpc_get_stats(self.h, _ptr(polishes), _stream_ptr(stream)),
                     "mpc_get_stats")
 
+    def get_pivots(self, pivots=None, stream=None):
+        self._check(self.lib.mpc_get_pivots(self.h, _ptr(pivots), _stream_ptr(stream)),
+                    "mpc_get_pivots")
+
+    def set_kernel_timing(self, enable: bool):
+        self._check(self.lib.mpc_set_kernel_timing(self.h, 1 if enable else 0), "mpc_set_kernel_timing")
+
+    def kernel_times(self, reset: bool = True):
+        """{class: (total ms, launches)} for the classes pack, factor, round, polish."""
+        ms = (ctypes.c_double * KERNEL_CLASSES)()
+        n = (ctypes.c_int64 * KERNEL_CLASSES)()
+        self._check(self.lib.mpc_get_kernel_times(self.h, ms, n, 1 if reset else 0), "mpc_get_kernel_times")
+        return {name: (ms[i], int(n[i])) for i, name in enumerate(KERNEL_CLASS_NAMES)}
+
     @property
     def workspace_bytes(self) -> int:
         return int(self.lib.mpc_workspace_bytes(self.h))
@@ -216,7 +240,7 @@ def solver_for(batch, **overrides) -> Solver:
 
 def solve_workload(batch, solver: Optional[Solver] = None, device="cuda", **overrides):
     """Solve every instance of ``batch`` on the GPU; returns numpy arrays
-    (xi [B,N,nx], u [B,N,nu], status, iters, kkt, active_bits, polishes)."""
+    (xi [B,N,nx], u [B,N,nu], status, iters, kkt, active_bits, polishes, pivots)."""
     import numpy as np
     import torch
     s = solver or solver_for(batch, **overrides)
@@ -232,9 +256,12 @@ def solve_workload(batch, solver: Optional[Solver] = None, device="cuda", **over
     kk = torch.empty(B, dtype=torch.float32, device=dev)
     bits = torch.empty((B, N), dtype=torch.int64, device=dev)
     npol = torch.empty(B, dtype=torch.int32, device=dev)
+    npiv = torch.empty(B, dtype=torch.int32, device=dev)
     s.get_traj(xi, u, st, it, kk, bits)
     s.get_stats(npol)
+    s.get_pivots(npiv)
     torch.cuda.synchronize(dev)
     return dict(xi=xi.cpu().numpy(), u=u.cpu().numpy(), status=st.cpu().numpy(),
                 iters=it.cpu().numpy(), kkt=kk.cpu().numpy(),
-                active_bits=bits.cpu().numpy().view(np.uint64), polishes=npol.cpu().numpy())
+                active_bits=bits.cpu().numpy().view(np.uint64), polishes=npol.cpu().numpy(),
+                pivots=npiv.cpu().numpy())
