@@ -36,7 +36,12 @@ KKT_TOL = 1e-5
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # dram bytes (read + write) per launch of a kernel class from one ncu capture,
 # keyed "class:source hash"; a changed source makes the entry stale (null)
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/polish_cta_kernel_walking_B4096_N20.md: round-0 launch (all 4096 instances)
+    "polish:3cfe95b24a0fd308": 293040128,
+    # profiles/round2_kernel_walking_B4096_N20.md: round-0 launch
+    "round:3cfe95b24a0fd308": 443067648,
+}
 
 
 def kernel_source_hash() -> str:
@@ -228,7 +233,7 @@ def run_gpu(args):
     world, rank, local = dist_env()
     # CPU baseline first: its spawned process pool starts before any GPU call (rank 0, N=1)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.device_only:
         n, el, w = oracle_sample(args.cpu_seconds, host_cores())
         cpu = {"value": n / el, "unit": "solves/s", "cores": w, "kind": "oracle",
                "sample": f"{n} instances of the same workload in {el:.1f} s (FP64 oracle, one process per core)"}
@@ -313,46 +318,48 @@ def run_gpu(args):
     ok = int(((status == 0) & (kkt <= KKT_TOL)).sum())
     value = world * ok / (ms_per_step / 1e3)
 
-    # end to end through the C ABI from pinned host buffers.  Two handles on
-    # two streams, as a serving loop would run them: the host-to-device copy
-    # (and packing) of batch k+1 is enqueued before the solve of batch k, so
-    # it overlaps that solve.  Every step still copies all of its inputs in
-    # and its results out inside the timed region.
-    h_in = pinmpc.device_inputs(batch, pin_host=True)
-    solvers = [solver, pinmpc.solver_for(batch, max_iter=args.max_iter)]
-    streams = [stream, torch.cuda.Stream(dev)]
+    e2e_val, h2d, d2h = None, 0, 0
+    if not args.device_only:
+        # end to end through the C ABI from pinned host buffers.  Two handles on
+        # two streams, as a serving loop would run them: the host-to-device copy
+        # (and packing) of batch k+1 is enqueued before the solve of batch k, so
+        # it overlaps that solve.  Every step still copies all of its inputs in
+        # and its results out inside the timed region.
+        h_in = pinmpc.device_inputs(batch, pin_host=True)
+        solvers = [solver, pinmpc.solver_for(batch, max_iter=args.max_iter)]
+        streams = [stream, torch.cuda.Stream(dev)]
 
-    def pinned_outputs():
-        return (torch.empty((B, N, 13), dtype=torch.float32).pin_memory(),
-                torch.empty((B, N, 24), dtype=torch.float32).pin_memory(),
-                torch.empty(B, dtype=torch.int32).pin_memory(),
-                torch.empty(B, dtype=torch.float32).pin_memory())
+        def pinned_outputs():
+            return (torch.empty((B, N, 13), dtype=torch.float32).pin_memory(),
+                    torch.empty((B, N, 24), dtype=torch.float32).pin_memory(),
+                    torch.empty(B, dtype=torch.int32).pin_memory(),
+                    torch.empty(B, dtype=torch.float32).pin_memory())
 
-    outs = [pinned_outputs(), pinned_outputs()]
-    h2d = sum(v.numel() * v.element_size() for v in h_in.values())
-    d2h = sum(v.numel() * v.element_size() for v in outs[0])
+        outs = [pinned_outputs(), pinned_outputs()]
+        h2d = sum(v.numel() * v.element_size() for v in h_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in outs[0])
 
-    def e2e_run(K):
-        solvers[0].set_stages(B, N, **h_in, stream=streams[0])
-        for k in range(K):
-            if k + 1 < K:
-                solvers[(k + 1) % 2].set_stages(B, N, **h_in, stream=streams[(k + 1) % 2])
-            sl = k % 2
-            solvers[sl].solve(B, stream=streams[sl])
-            o = outs[sl]
-            solvers[sl].get_traj(o[0], o[1], o[2], None, o[3], None, stream=streams[sl])
-        for sx in streams:
-            sx.synchronize()
+        def e2e_run(K):
+            solvers[0].set_stages(B, N, **h_in, stream=streams[0])
+            for k in range(K):
+                if k + 1 < K:
+                    solvers[(k + 1) % 2].set_stages(B, N, **h_in, stream=streams[(k + 1) % 2])
+                sl = k % 2
+                solvers[sl].solve(B, stream=streams[sl])
+                o = outs[sl]
+                solvers[sl].get_traj(o[0], o[1], o[2], None, o[3], None, stream=streams[sl])
+            for sx in streams:
+                sx.synchronize()
 
-    e2e_run(args.warmup)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_run(args.steps)
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    last = outs[(args.steps - 1) % 2]
-    e2e_ok = int(((last[2].numpy() == 0) & (last[3].numpy() <= KKT_TOL)).sum())
-    e2e_val = world * e2e_ok / e2e_s
+        e2e_run(args.warmup)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_run(args.steps)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        last = outs[(args.steps - 1) % 2]
+        e2e_ok = int(((last[2].numpy() == 0) & (last[3].numpy() <= KKT_TOL)).sum())
+        e2e_val = world * e2e_ok / e2e_s
 
     if rank != 0:
         return
@@ -377,7 +384,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "global_batch": world * B, "horizon": N, "seed": SEED,
                    "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
                    "max_iter": args.max_iter},
-        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                if e2e_val is not None else None),
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
@@ -391,6 +399,8 @@ def run_gpu(args):
                         "kkt_max": float(kkt.max()), "polishes_mean": float(polishes.mean()),
                         "free_pivots_mean": float(pivots.mean())},
     }
+    if args.device_only:
+        line["note"] = "device-only profiling run (--device-only): not a bench result"
     print(json.dumps(line), flush=True)
 
 
@@ -404,6 +414,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--device-only", action="store_true",
+                    help="profiling aid: only the device-resident steps (no CPU baseline, no e2e leg); "
+                         "the line it prints is not a bench result")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
