@@ -156,14 +156,17 @@ def _oracle_chunk(spec, start, n):
     from paper_2606_05687_b300 import workload as W
     ids = [(start + i) % spec.B for i in range(n)]
     batch = W.generate(spec, instances=ids)
+    sols = []
     for b in range(len(ids)):
-        qp.solve_instance(qp.instance(batch, b))
-    return len(ids)
+        sol = qp.solve_instance(qp.instance(batch, b))
+        sols.append((ids[b], sol.xi, sol.u))
+    return sols
 
 
 def oracle_sample(seconds: float, workers: int, start: int = 0):
     """Time the FP64 oracle (as it stands) on instances start, start+1, ... of
-    the benchmark workload for about `seconds`; returns (solves, elapsed, workers)."""
+    the benchmark workload for about `seconds`; returns (solves, elapsed,
+    workers, {instance: (xi, u)} of the oracle's solutions)."""
     import multiprocessing as mp
     from concurrent.futures import FIRST_COMPLETED, ProcessPoolExecutor, wait
     from paper_2606_05687_b300 import workload as W
@@ -174,6 +177,7 @@ def oracle_sample(seconds: float, workers: int, start: int = 0):
     print(f"[bench] oracle sample: {workers} worker processes, ~{seconds:.0f} s", file=sys.stderr, flush=True)
     chunk = 4
     done = 0
+    refs = {}
     nxt = start
     with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         list(ex.map(_oracle_warm, range(workers)))   # imports outside the timed window
@@ -187,13 +191,16 @@ def oracle_sample(seconds: float, workers: int, start: int = 0):
             if not fin:
                 raise RuntimeError("oracle worker pool made no progress in 120 s")
             for f in fin:
-                done += f.result()
+                res = f.result()
+                done += len(res)
+                for b, xi, u in res:
+                    refs.setdefault(b, (xi, u))
             if time.perf_counter() - t0 < seconds:
                 while len(pend) < 2 * workers:
                     pend.add(ex.submit(_oracle_chunk, spec, nxt % B_BENCH, chunk))
                     nxt += chunk
         elapsed = time.perf_counter() - t0
-    return done, elapsed, workers
+    return done, elapsed, workers, refs
 
 
 def host_cores() -> int:
@@ -210,7 +217,7 @@ def run_reference(args):
     cores = host_cores()
     per_step, total = [], 0
     for s in range(args.warmup + args.steps):
-        n, el, _ = oracle_sample(args.ref_seconds, cores, start=64 * s)
+        n, el, _, _ = oracle_sample(args.ref_seconds, cores, start=64 * s)
         if s >= args.warmup:
             per_step.append(n / el)
             total += n
@@ -233,8 +240,9 @@ def run_gpu(args):
     world, rank, local = dist_env()
     # CPU baseline first: its spawned process pool starts before any GPU call (rank 0, N=1)
     cpu = None
+    refs = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.device_only:
-        n, el, w = oracle_sample(args.cpu_seconds, host_cores())
+        n, el, w, refs = oracle_sample(args.cpu_seconds, host_cores())
         cpu = {"value": n / el, "unit": "solves/s", "cores": w, "kind": "oracle",
                "sample": f"{n} instances of the same workload in {el:.1f} s (FP64 oracle, one process per core)"}
     if world > 1:
@@ -271,6 +279,8 @@ def run_gpu(args):
         if ev is not None:
             ev[2].record(stream)
         solver.get_traj(xi, u, st, it, kk, bits, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -286,7 +296,7 @@ def run_gpu(args):
     # records around each of its launches on `stream`
     solver.kernel_times(reset=True)
     solver.set_kernel_timing(True)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     e_start = torch.cuda.Event(enable_timing=True)
     e_end = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -300,6 +310,7 @@ def run_gpu(args):
     solver.set_kernel_timing(False)
     solve_ms = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
     pack_ms = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
+    step_ms = [evs[s][0].elapsed_time(evs[s][3]) for s in range(args.steps)]
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([total_ms], device=dev)
@@ -399,6 +410,22 @@ def run_gpu(args):
                         "kkt_max": float(kkt.max()), "polishes_mean": float(polishes.mean()),
                         "free_pivots_mean": float(pivots.mean())},
     }
+    # served latency of a batch: set_stages -> get_traj complete, per timed step
+    line["latency_ms"] = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                          "what": f"one batch of {B} solves, set_stages to get_traj complete (device events)"}
+    if refs:
+        # per-instance error of the last timed step against the oracle's solutions
+        # of the instances the CPU baseline leg solved (same workload, same seed)
+        xi_h, u_h = xi.cpu().numpy().astype(np.float64), u.cpu().numpy().astype(np.float64)
+        eu, ex = [], []
+        for b, (xi_r, u_r) in refs.items():
+            nb = int(batch.horizon[b])
+            eu.append(np.abs(u_h[b, :nb] - u_r).max() / max(np.abs(u_r).max(), 1e-9))
+            ex.append(np.abs(xi_h[b, :nb] - xi_r).max() / max(np.abs(xi_r).max(), 1e-9))
+        line["oracle_error"] = {"instances": len(refs), "u_rel_max": float(np.max(eu)),
+                                "u_rel_p99": float(np.percentile(eu, 99)), "xi_rel_max": float(np.max(ex)),
+                                "xi_rel_p99": float(np.percentile(ex, 99)),
+                                "note": "relative to the oracle's max |u|, |xi| per instance; bar 1e-4"}
     if args.device_only:
         line["note"] = "device-only profiling run (--device-only): not a bench result"
     print(json.dumps(line), flush=True)

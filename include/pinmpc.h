@@ -141,7 +141,9 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out);
 mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream);
 
 /* Solve instances [0, B) of the last set_stages batch on `stream`
- * (asynchronous).  Convergence is reported per instance, not here. */
+ * (asynchronous: the whole round schedule up to max_iter is enqueued and the
+ * call returns without waiting; instances that finish leave the later
+ * rounds' work lists).  Convergence is reported per instance, not here. */
 mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream);
 
 /* Copy results of the last solve to caller buffers (device or host; any

@@ -507,11 +507,9 @@ __device__ void round_fail(const RoundArgs& a, int b, int status) {
 // One round of ADMM iterations (a.m0, a.m1] for one instance per CTA; the
 // factor cache and the iterate stay in global memory between rounds.
 template <class D, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float* smem) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     constexpr bool TWO = RegT<D>::kTwo;
-    const int b = blockIdx.x;
     if (a.done[b]) return;
     const RoundSmem<D> L(a.N);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -682,6 +680,19 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
         sc[RoundState<D>::sWgt] = wgt;
         sc[RoundState<D>::sRestart] = restart ? 1.0f : 0.0f;
         sc[RoundState<D>::sCb] = __int_as_float(cb);
+    }
+}
+
+// One round of ADMM iterations (a.m0, a.m1]: persistent CTAs (one per SM), each
+// taking instances of the round's list until it is exhausted.
+template <class D, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int item;
+    for (;;) {
+        const int b = next_instance(a, 0, &item);
+        if (b < 0) break;
+        round_instance<D, MAXT>(a, b, smem);
     }
 }
 

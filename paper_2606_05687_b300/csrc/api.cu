@@ -37,6 +37,7 @@ struct Shape {
     int (*round_smem)(int N);
     int (*cache_floats)(int N);
     void (*launch_factor)(const FactorArgs&, cudaStream_t);
+    int (*resident_per_sm)(int kernel, int N, int smem);  // kernel 0 round, 1 polish
 };
 
 template <class D>
@@ -83,11 +84,27 @@ void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
     polish_cta_kernel<D><<<B, kPT, smem, s>>>(a);
 }
 template <class D>
+int resident_per_sm_t(int kernel, int N, int smem) {
+    int n = 0;
+    cudaError_t e;
+    if (kernel == 0) {
+        if (N <= 20) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, round2_kernel<D, 640>, 32 * N, smem);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, round2_kernel<D, 1024>, 32 * N, smem);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, polish_cta_kernel<D>, kPT, smem);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
+template <class D>
 Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
                  launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
-                 cache_floats_t<D>, launch_factor_t<D>};
+                 cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -129,8 +146,9 @@ struct mpc_handle {
     uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
     int* done = nullptr;         // [B_max]
     int* flags = nullptr;        // [B_max] input-check bits of the factor kernel
-    int* active = nullptr;       // running-instance counter
-    int* active_host = nullptr;  // pinned host copy of the counter
+    int* lists = nullptr;        // [2][B_max] instances still running, by round parity
+    int* work = nullptr;         // [4] round cursor, polish cursor, list counts [2]
+    int sms = 0;                 // streaming multiprocessors of the device
     float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
     float* staging = nullptr;  // device copies of host-memory inputs
     size_t staging_floats = 0;
@@ -329,6 +347,10 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     mpc_handle* h = new (std::nothrow) mpc_handle();
     if (!h) return fail(nullptr, MPC_ERR_OOM, "host allocation failed");
     h->cfg = c;
+    if (cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, c.device) != cudaSuccess || h->sms < 1) {
+        cudaGetLastError();
+        h->sms = 1;
+    }
     h->shape = sh;
     h->nc = c.n_contacts;
     h->nu = c.n_contacts * c.contact_dim;
@@ -363,8 +385,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->modes, modes_b) == cudaSuccess && cudaMalloc(&h->lastm, modes_b) == cudaSuccess &&
               cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->flags, B * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&h->active, sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess &&
-              cudaMallocHost(&h->active_host, sizeof(int)) == cudaSuccess;
+              cudaMalloc(&h->lists, 2 * B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->work, 4 * sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         const unsigned long long want = h->bytes;
@@ -464,7 +486,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
     r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
     r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
-    r.done = h->done; r.active = h->active; r.Kst = h->Kst; r.flags = h->flags;
+    r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
     const int round_smem = h->shape.round_smem(h->N_set);
@@ -481,11 +503,18 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         if ((e = timed_launch(h, kClassFactor, st, [&] { h->shape.launch_factor(fa, st); })) != cudaSuccess)
             return cuda_fail(h, e, "factor kernel launch");
     }
-    // rounds of ADMM iterations, each followed by the polish/certify kernel;
-    // stop once no instance is running (host reads the counter each round)
-    int m0 = 0;
+    // rounds of ADMM iterations, each followed by the polish/certify kernel,
+    // all enqueued up front (no host synchronisation): the round kernel's
+    // persistent CTAs work through the round's list of running instances and
+    // the polish kernel's CTAs index it, so a round with few or no instances
+    // left costs one short launch of each kernel
+    int* cursor = h->work;
+    int* cnt = h->work + 2;
+    const int round_grid = std::max(1, std::min(B, h->sms * h->shape.resident_per_sm(0, h->N_set, round_smem)));
+    const int polish_grid = B;
+    int m0 = 0, round = 0;
     double interval = c.check_every;
-    for (;;) {
+    for (;; ++round) {
         int m1;
         if (m0 == 0) {
             m1 = std::min(c.check_start, c.max_iter);
@@ -493,18 +522,22 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
             m1 = (int)std::min<double>((double)m0 + interval, (double)c.max_iter);
             interval *= c.check_growth;
         }
+        const int in = round & 1, out = in ^ 1;
         r.m0 = m0;
         r.m1 = m1;
-        if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_round(r, B, round_smem, st); })) != cudaSuccess)
+        r.list_in = round == 0 ? nullptr : h->lists + (size_t)in * c.B_max;
+        r.cnt_in = cnt + in;
+        r.list_out = h->lists + (size_t)out * c.B_max;
+        r.cnt_out = cnt + out;
+        r.cursor = cursor;
+        if ((e = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(cnt + out, 0, sizeof(int), st)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaMemsetAsync");
+        if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_round(r, round_grid, round_smem, st); })) != cudaSuccess)
             return cuda_fail(h, e, "round kernel launch");
-        if ((e = cudaMemsetAsync(h->active, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
-        if ((e = timed_launch(h, kClassPolish, st, [&] { h->shape.launch_polish(r, B, polish_smem, st); })) != cudaSuccess)
+        if ((e = timed_launch(h, kClassPolish, st, [&] { h->shape.launch_polish(r, polish_grid, polish_smem, st); })) != cudaSuccess)
             return cuda_fail(h, e, "polish kernel launch");
         if (m1 >= c.max_iter) break;
-        if ((e = cudaMemcpyAsync(h->active_host, h->active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return cuda_fail(h, e, "cudaMemcpyAsync (counter)");
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-        if (*h->active_host == 0) break;
         m0 = m1;
     }
     h->have_solution = true;
@@ -611,9 +644,9 @@ void mpc_destroy(mpc_handle* h) {
     cudaFree(h->lastm);
     cudaFree(h->done);
     cudaFree(h->flags);
-    cudaFree(h->active);
+    cudaFree(h->lists);
+    cudaFree(h->work);
     cudaFree(h->Kst);
-    cudaFreeHost(h->active_host);
     cudaFree(h->staging);
     cudaGetLastError();
     delete h;

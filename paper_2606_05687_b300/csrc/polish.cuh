@@ -31,7 +31,15 @@ struct RoundArgs {
     uint32_t* modes;         // [B][N][NC] faces of the latest z
     uint32_t* lastm;         // [B][N][NC] faces of the last polished z
     int* done;               // [B] 1 once the instance has its final output
-    int* active;             // count of instances still running after this round
+    // work of this round (persistent CTAs take instances from a cursor):
+    // list_in[i], i < *cnt_in, or every i < B when list_in is null (round 0);
+    // the polish appends the instances still running to list_out / *cnt_out
+    const int* list_in;
+    const int* cnt_in;
+    int B;
+    int* list_out;
+    int* cnt_out;
+    int* cursor;             // [2] work cursors of the round and polish kernels, zeroed per round
     float* Kst;              // [B][N][NU][NX+1] polish gains
     float* out_xi;
     float* out_u;
@@ -42,6 +50,20 @@ struct RoundArgs {
     int* out_npol;
     int* out_piv;            // [B] free pivots eliminated by the polish
 };
+
+// Next instance for a persistent CTA (all threads get the same value), or -1
+// when the round's list is exhausted; `which` selects the kernel's cursor.
+// Starts with a barrier, so the CTA's shared memory is free for the next item.
+__device__ __forceinline__ int next_instance(const RoundArgs& a, int which, int* slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int i = atomicAdd(a.cursor + which, 1);
+        const int n = a.list_in ? *a.cnt_in : a.B;
+        *slot = (i < n) ? (a.list_in ? a.list_in[i] : i) : -1;
+    }
+    __syncthreads();
+    return *slot;
+}
 
 // Column i of the reduced input map of one stage (lane i < NU), from the
 // stage's record s in shared memory:

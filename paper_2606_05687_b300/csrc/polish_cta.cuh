@@ -713,10 +713,8 @@ __device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, in
 
 // Polish / certify / refine after a round: one CTA per instance.
 template <class D>
-__global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(RoundArgs a) {
-    extern __shared__ __align__(16) float psm[];
+__device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float* psm) {
     constexpr int NX = D::NX, NU = D::NU;
-    const int b = blockIdx.x;
     if (a.done[b]) return;
     CCtx<D> c(a.N);
     c.sm = psm;
@@ -784,8 +782,19 @@ __global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(Rou
     }
     if (c.tid == 0) {
         a.out_npol[b] = npol;
-        atomicAdd(a.active, 1);
+        a.list_out[atomicAdd(a.cnt_out, 1)] = b;  // still running: next round
     }
+}
+
+// Polish / certify / refine after a round: CTA i takes slot i of the round's
+// list (grid = batch size; slots past the list's length return at once).
+template <class D>
+__global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(RoundArgs a) {
+    extern __shared__ __align__(16) float psm[];
+    const int i = blockIdx.x;
+    const int b = a.list_in ? (i < *a.cnt_in ? a.list_in[i] : -1) : (i < a.B ? i : -1);
+    if (b < 0) return;
+    polish_instance<D>(a, b, psm);
 }
 
 }  // namespace pinmpc
