@@ -275,7 +275,7 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->rho = 100.0f;
     cfg->u_scale = 300.0f;
     cfg->max_iter = 1000;
-    cfg->kkt_tol = 5e-6f;
+    cfg->kkt_tol = 2e-6f;
     cfg->check_start = 12;
     cfg->check_every = 20;
     cfg->check_growth = 2.0f;

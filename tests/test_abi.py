@@ -57,7 +57,7 @@ def test_struct_layout_matches_header(tmp_path, P):
 
 def test_defaults_and_limits(P):
     cfg = P.default_config(13, 8, 3, 4096, 20)
-    assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(5e-6)
+    assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(2e-6)
     assert cfg.polish == 1 and cfg.accel == 1
     lib = P.load()
     assert lib.mpc_max_horizon(13, 24) >= 20
