@@ -169,6 +169,19 @@ mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status,
  * or host pointer; host pointers synchronize `stream`. */
 mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream);
 
+/* Receding-horizon warm start: the next mpc_solve_batch starts instances
+ * [0, B) of the last solve from their final ADMM iterate (z, v and the
+ * scaled duals theta, beta, lambda) moved `shift` stages towards the start of
+ * each instance's horizon, the last stage repeated into the freed tail, with
+ * the acceleration restarted; shift 0 re-solves from the final iterate.
+ * Call after mpc_solve_batch and before (or after) mpc_set_stages of the next
+ * batch, with the same horizon stride N; one solve consumes it.  A warm start
+ * changes the iterate the method starts from, not the problem: the certified
+ * solution is the same (same tolerance).  Requires a previous solve
+ * (MPC_ERR_STATE) and 0 <= shift < N (MPC_ERR_INVALID_ARG).  The paper solves
+ * each MPC step cold; this is the standard receding-horizon practice. */
+mpc_status mpc_warm_start(mpc_handle* h, int32_t shift, void* stream);
+
 /* Free pivots the polish eliminated in the last solve, per instance [B]:
  * summed over its Riccati scans, the number of free input components of
  * every stage (the elimination steps actually run).  A work count for

@@ -573,14 +573,16 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         float4* fd = reinterpret_cast<float4*>(c.fac);
         for (int e = tid; e < Nh * 2 * NX * FR / 4; e += nthr) fd[e] = fs[e];
     }
+    const bool warm = a.m0 == 0 && b < a.warm_B;  // start from the shifted previous iterate
     if (a.m0 == 0) {
-        for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
+        if (!warm) for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
         for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
         if (tid == 0) {
             a.out_npol[b] = 0;
             a.out_piv[b] = 0;
         }
-    } else {
+    }
+    if (a.m0 > 0 || warm) {
         const float4* src = reinterpret_cast<const float4*>(gstate);
         float4* dst = reinterpret_cast<float4*>(c.var);
         for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
@@ -628,7 +630,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     float alpha = 1.0f, cprev = INFINITY, wgt = 0.0f;
     bool restart = false;
     int cb = 0;
-    if (a.m0 > 0) {
+    if (a.m0 > 0 || warm) {
         const float* sc = gstate + nvar;
         alpha = sc[RoundState<D>::sAlpha];
         cprev = sc[RoundState<D>::sCprev];
@@ -680,6 +682,42 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         sc[RoundState<D>::sWgt] = wgt;
         sc[RoundState<D>::sRestart] = restart ? 1.0f : 0.0f;
         sc[RoundState<D>::sCb] = __int_as_float(cb);
+    }
+}
+
+// Receding-horizon warm start: the final
+// ADMM iterate of instance b -- both buffers of (z, v, theta, beta, lambda) --
+// moves `shift` stages towards the start of its horizon Nh, the last stage
+// repeated into the freed tail, and the acceleration restarts (alpha 1, no
+// previous residual).  One CTA per instance, through shared memory.
+template <class D>
+__global__ void warm_shift_kernel(float* state, const float* rec, int irec, int n_rec, int N, int shift) {
+    extern __shared__ __align__(16) float wsm[];
+    const int b = blockIdx.x;
+    float* st = state + (size_t)b * RoundState<D>::floats(N);
+    const int nvar = RoundState<D>::var_floats(N);
+    const float* tail = rec + (size_t)b * irec + (size_t)n_rec * D::SREC;
+    const int Nh0 = __float_as_int(__ldg(tail + D::tH));
+    const int Nh = (Nh0 >= 1 && Nh0 <= N) ? Nh0 : N;
+    bool bad = false;
+    for (int e = threadIdx.x; e < nvar; e += blockDim.x) {
+        wsm[e] = st[e];
+        bad |= !isfinite(wsm[e]);
+    }
+    // an instance without a usable iterate (its previous solve failed) starts cold
+    const bool cold = __syncthreads_or(bad);
+    constexpr int SV = 5 * D::NBP;  // floats of one stage in one buffer
+    for (int e = threadIdx.x; e < nvar; e += blockDim.x) {
+        const int buf = e / (N * SV), r = e % (N * SV), j = r / SV, o = r % SV;
+        const int src = min(j + shift, Nh - 1);
+        st[e] = cold ? 0.0f : (j < Nh ? wsm[(buf * N + src) * SV + o] : wsm[e]);
+    }
+    if (threadIdx.x == 0) {
+        float* sc = st + nvar;
+        sc[RoundState<D>::sAlpha] = 1.0f;
+        sc[RoundState<D>::sCprev] = INFINITY;
+        sc[RoundState<D>::sWgt] = 0.0f;
+        sc[RoundState<D>::sRestart] = 0.0f;
     }
 }
 

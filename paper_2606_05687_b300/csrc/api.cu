@@ -38,6 +38,9 @@ struct Shape {
     int (*cache_floats)(int N);
     void (*launch_factor)(const FactorArgs&, cudaStream_t);
     int (*resident_per_sm)(int kernel, int N, int smem);  // kernel 0 round, 1 polish
+    void (*launch_warm_shift)(float* state, const float* rec, int irec, int n_rec, int B, int N, int shift,
+                              cudaStream_t s);
+    cudaError_t (*set_warm_attr)(int bytes);
 };
 
 template <class D>
@@ -100,11 +103,20 @@ int resident_per_sm_t(int kernel, int N, int smem) {
     return n > 0 ? n : 1;
 }
 template <class D>
+void launch_warm_shift_t(float* state, const float* rec, int irec, int n_rec, int B, int N, int shift, cudaStream_t s) {
+    warm_shift_kernel<D><<<B, 256, RoundState<D>::var_floats(N) * sizeof(float), s>>>(state, rec, irec, n_rec, N, shift);
+}
+template <class D>
+cudaError_t set_warm_attr_t(int bytes) {
+    return cudaFuncSetAttribute(warm_shift_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <class D>
 Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
                  launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
-                 cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>};
+                 cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>, launch_warm_shift_t<D>,
+                 set_warm_attr_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -149,6 +161,7 @@ struct mpc_handle {
     int* lists = nullptr;        // [2][B_max] instances still running, by round parity
     int* work = nullptr;         // [4] round cursor, polish cursor, list counts [2]
     int sms = 0;                 // streaming multiprocessors of the device
+    int warm_B = 0, warm_N = 0;  // a warm start is pending for instances [0, warm_B) at horizon stride warm_N
     float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
     float* staging = nullptr;  // device copies of host-memory inputs
     size_t staging_floats = 0;
@@ -530,6 +543,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         r.list_out = h->lists + (size_t)out * c.B_max;
         r.cnt_out = cnt + out;
         r.cursor = cursor;
+        r.warm_B = (h->warm_N == h->N_set) ? std::min(h->warm_B, B) : 0;
         if ((e = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(cnt + out, 0, sizeof(int), st)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemsetAsync");
@@ -542,6 +556,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     }
     h->have_solution = true;
     h->B_solved = B;
+    h->warm_B = 0;  // a warm start is consumed by one solve
     return MPC_OK;
 }
 
@@ -595,6 +610,22 @@ mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream) {
         if (is_host_pointer(pivots) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaStreamSynchronize");
     }
+    return MPC_OK;
+}
+
+mpc_status mpc_warm_start(mpc_handle* h, int32_t shift, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_solution) return fail(h, MPC_ERR_STATE, "mpc_warm_start before mpc_solve_batch");
+    if (shift < 0 || shift >= h->N_set) return fail(h, MPC_ERR_INVALID_ARG, "shift=%d outside [0, N=%d)", shift, h->N_set);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const int smem = h->shape.state_floats(h->N_set) * (int)sizeof(float);
+    if (smem > 48 * 1024 && (e = h->shape.set_warm_attr(smem)) != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+    h->shape.launch_warm_shift(h->state, h->rec, h->irec, h->cfg.N_max, h->B_solved, h->N_set, shift, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "warm-start kernel launch");
+    h->warm_B = h->B_solved;
+    h->warm_N = h->N_set;
     return MPC_OK;
 }
 

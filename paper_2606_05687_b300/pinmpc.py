@@ -71,6 +71,8 @@ def load() -> ctypes.CDLL:
     lib.mpc_get_traj.restype = ctypes.c_int
     lib.mpc_get_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mpc_get_stats.restype = ctypes.c_int
+    lib.mpc_warm_start.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+    lib.mpc_warm_start.restype = ctypes.c_int
     lib.mpc_get_pivots.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mpc_get_pivots.restype = ctypes.c_int
     lib.mpc_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int32]
@@ -172,6 +174,10 @@ class Solver:
     def get_stats(self, polishes=None, stream=None):
         self._check(self.lib.mpc_get_stats(self.h, _ptr(polishes), _stream_ptr(stream)),
                     "mpc_get_stats")
+
+    def warm_start(self, shift: int = 1, stream=None):
+        """Start the next solve from the last solve's final iterate shifted by `shift` stages."""
+        self._check(self.lib.mpc_warm_start(self.h, int(shift), _stream_ptr(stream)), "mpc_warm_start")
 
     def get_pivots(self, pivots=None, stream=None):
         self._check(self.lib.mpc_get_pivots(self.h, _ptr(pivots), _stream_ptr(stream)),

@@ -132,6 +132,21 @@ class Batch:
               if f.name != "spec"}
         return Batch(spec=dataclasses.replace(self.spec, B=len(idx)), **kw)
 
+    def receding(self, xi0: np.ndarray, u_prev: np.ndarray) -> "Batch":
+        """The next MPC step of a receding horizon: every stage array moves one
+        stage towards the start (the last stage repeated), with the given
+        initial state and previous input (float32 [B,nx], [B,nu])."""
+        kw = {}
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            if f.name in ("spec", "xi0", "u_prev", "horizon", "nu_arr"):
+                kw[f.name] = v
+            else:
+                kw[f.name] = np.concatenate([v[:, 1:], v[:, -1:]], axis=1)
+        kw["xi0"] = np.ascontiguousarray(xi0, dtype=np.float32)
+        kw["u_prev"] = np.ascontiguousarray(u_prev, dtype=np.float32)
+        return Batch(**kw)
+
     def stance(self) -> np.ndarray:
         """bool [B,N,nc]: contact c of stage k is in stance."""
         bits = (self.mask[..., None] >> np.arange(self.nc, dtype=np.uint32)) & 1

@@ -33,3 +33,17 @@ def test_model_structure():
     st = b.stance()
     assert np.array_equal(st[..., 0:4].min(-1), st[..., 0:4].max(-1))
     assert 0.3 < st.mean() < 0.9
+
+
+def test_receding_step_shifts_stages():
+    b = W.generate(W.rl_scale_walking(B=4, N=6, seed=1002))
+    xi0 = np.arange(4 * b.nx, dtype=np.float32).reshape(4, b.nx)
+    up = np.ones((4, b.nu), np.float32)
+    n = b.receding(xi0, up)
+    assert n.B == b.B and n.N == b.N
+    for name in ("A", "Bm", "e", "Q", "R", "ry", "ru", "mu", "fmax", "mask"):
+        old, new = getattr(b, name), getattr(n, name)
+        assert np.array_equal(new[:, :-1], old[:, 1:]), name
+        assert np.array_equal(new[:, -1], old[:, -1]), name
+    assert np.array_equal(n.xi0, xi0) and np.array_equal(n.u_prev, up)
+    assert np.array_equal(n.horizon, b.horizon)
