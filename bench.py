@@ -4,11 +4,14 @@ One step = one pass of the whole hot path over one batch of the walking
 workload (B=4096 environments, horizon N=20, 8 point contacts, nu=24):
 mpc_set_stages (pack/scale) + mpc_solve_batch (caches, ADMM, polish,
 certificate, outputs) + mpc_get_traj, inputs resident in HBM.  Only solves
-whose KKT certificate is <= 1e-5 count.  `e2e` repeats the step through the
-same C ABI from pinned host buffers with the host<->device copies inside the
-timed region, on two handles and two streams so that the copy of batch k+1
-overlaps the solve of batch k.  `--impl reference` times the FP64 CPU oracle
-on a bounded sample of the same workload.
+whose KKT certificate is <= 1e-5 count.  Consecutive steps alternate between
+two handles on two streams (two batches in flight), so one batch's packing
+and first round overlap the previous batch's last rounds; `single_stream`
+reports the same steps with one batch in flight.  `e2e` repeats the steps
+through the same C ABI from pinned host buffers with the host<->device
+copies inside the timed region (the copy of batch k+1 overlaps the solve of
+batch k).  `--impl reference` times the FP64 CPU oracle on a bounded sample
+of the same workload.
 
 Launch:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
          (N > 1 under torch.distributed.run: weak scaling, one batch per rank)
@@ -31,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPC QP solves/s at B=4096 N=20 (KKT≤1e-5); served p50/p99 solve latency"
 B_BENCH, N_BENCH, SEED = 4096, 20, 1002
+INFLIGHT = 2  # batches in flight on separate handles and streams
 KKT_TOL = 1e-5
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -273,29 +277,39 @@ def run_gpu(args):
     spec = W.rl_scale_walking(B=B_BENCH, N=N_BENCH, seed=SEED + 7919 * rank)
     batch = W.generate(spec)
     B, N = batch.B, batch.N
-    solver = pinmpc.solver_for(batch, max_iter=args.max_iter)
-    stream = torch.cuda.current_stream(dev)
+    # INFLIGHT batches on as many handles and streams: batch k+1's packing,
+    # factors and first round overlap batch k's last rounds, which keep only
+    # a few instances busy (the way a batched-solve service runs)
+    solvers = [pinmpc.solver_for(batch, max_iter=args.max_iter) for _ in range(INFLIGHT)]
+    solver = solvers[0]
+    streams = [torch.cuda.current_stream(dev)] + [torch.cuda.Stream(dev) for _ in range(INFLIGHT - 1)]
+    stream = streams[0]
     t = pinmpc.device_inputs(batch, dev)
-    xi = torch.empty((B, N, 13), dtype=torch.float32, device=dev)
-    u = torch.empty((B, N, 24), dtype=torch.float32, device=dev)
-    st = torch.empty(B, dtype=torch.int32, device=dev)
-    it = torch.empty(B, dtype=torch.int32, device=dev)
-    kk = torch.empty(B, dtype=torch.float32, device=dev)
-    bits = torch.empty((B, N), dtype=torch.int64, device=dev)
-    npol = torch.empty(B, dtype=torch.int32, device=dev)
 
-    def step(ev=None):
+    def device_outputs():
+        return dict(xi=torch.empty((B, N, 13), dtype=torch.float32, device=dev),
+                    u=torch.empty((B, N, 24), dtype=torch.float32, device=dev),
+                    st=torch.empty(B, dtype=torch.int32, device=dev),
+                    it=torch.empty(B, dtype=torch.int32, device=dev),
+                    kk=torch.empty(B, dtype=torch.float32, device=dev),
+                    bits=torch.empty((B, N), dtype=torch.int64, device=dev))
+
+    outs_d = [device_outputs() for _ in range(INFLIGHT)]
+
+    def step(k, nslots, ev=None):
+        sl = k % nslots
+        sv, sx, o = solvers[sl], streams[sl], outs_d[sl]
         if ev is not None:
-            ev[0].record(stream)
-        solver.set_stages(B, N, **t, stream=stream)
+            ev[0].record(sx)
+        sv.set_stages(B, N, **t, stream=sx)
         if ev is not None:
-            ev[1].record(stream)
-        solver.solve(B, stream=stream)
+            ev[1].record(sx)
+        sv.solve(B, stream=sx)
         if ev is not None:
-            ev[2].record(stream)
-        solver.get_traj(xi, u, st, it, kk, bits, stream=stream)
+            ev[2].record(sx)
+        sv.get_traj(o["xi"], o["u"], o["st"], o["it"], o["kk"], o["bits"], stream=sx)
         if ev is not None:
-            ev[3].record(stream)
+            ev[3].record(sx)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -304,53 +318,74 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    # per-kernel device times of the timed steps: event pairs the library
-    # records around each of its launches on `stream`
-    solver.kernel_times(reset=True)
-    solver.set_kernel_timing(True)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    e_start = torch.cuda.Event(enable_timing=True)
-    e_end = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
+    def timed_loop(nslots, with_events):
+        """`args.steps` steps over nslots handles; returns (total ms, per-step events)."""
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_end = torch.cuda.Event(enable_timing=True)
         e_start.record(stream)
-        for s in range(args.steps):
-            step(evs[s])
+        for sx in streams[1:nslots]:
+            sx.wait_stream(stream)
+        for k in range(args.steps):
+            step(k, nslots, evs[k] if with_events else None)
+        for sx in streams[1:nslots]:
+            stream.wait_stream(sx)
         e_end.record(stream)
         barrier()
-    total_ms = e_start.elapsed_time(e_end)
+        return e_start.elapsed_time(e_end), evs
+
+    # one batch in flight: the per-kernel device times come from these steps,
+    # where no launch overlaps another (the library records an event pair
+    # around each of its launches on the launching stream)
+    for k in range(args.warmup):
+        step(k, 1)
+    barrier()
+    solver.kernel_times(reset=True)
+    solver.set_kernel_timing(True)
+    with Clocks(local) as clk1:
+        single_ms, evs1 = timed_loop(1, True)
     ktimes = solver.kernel_times(reset=True)
     solver.set_kernel_timing(False)
-    solve_ms = [evs[s][1].elapsed_time(evs[s][2]) for s in range(args.steps)]
-    pack_ms = [evs[s][0].elapsed_time(evs[s][1]) for s in range(args.steps)]
+    solve_ms = [evs1[s][1].elapsed_time(evs1[s][2]) for s in range(args.steps)]
+    pack_ms = [evs1[s][0].elapsed_time(evs1[s][1]) for s in range(args.steps)]
+    step1_ms = [evs1[s][0].elapsed_time(evs1[s][3]) for s in range(args.steps)]
+    # INFLIGHT batches in flight: the headline figure
+    for k in range(args.warmup):
+        step(k, INFLIGHT)
+    barrier()
+    with Clocks(local) as clk:
+        total_ms, evs = timed_loop(INFLIGHT, True)
     step_ms = [evs[s][0].elapsed_time(evs[s][3]) for s in range(args.steps)]
-    ms_per_step = total_ms / args.steps
+    last = (args.steps - 1) % INFLIGHT
+    npol = torch.empty(B, dtype=torch.int32, device=dev)
     npiv = torch.empty(B, dtype=torch.int32, device=dev)
-    solver.get_stats(npol, stream=stream)
-    solver.get_pivots(npiv, stream=stream)
+    solvers[last].get_stats(npol, stream=streams[last])
+    solvers[last].get_pivots(npiv, stream=streams[last])
     torch.cuda.synchronize(dev)
+    o = outs_d[last]
+    xi, u = o["xi"], o["u"]
     polishes = npol.cpu().numpy()
     pivots = npiv.cpu().numpy()
-    status = st.cpu().numpy()
-    iters = it.cpu().numpy()
-    kkt = kk.cpu().numpy()
+    status = o["st"].cpu().numpy()
+    iters = o["it"].cpu().numpy()
+    kkt = o["kk"].cpu().numpy()
     ok = int(((status == 0) & (kkt <= KKT_TOL)).sum())
     total_s, ok_job = job_totals(world, total_ms / 1e3, ok, dev)
     ms_per_step = total_s * 1e3 / args.steps
     value = ok_job / (ms_per_step / 1e3)
+    single_s, _ = job_totals(world, single_ms / 1e3, ok, dev)
+    single = {"ms_per_step": single_s * 1e3 / args.steps, "value": ok_job / (single_s / args.steps),
+              "latency_ms": {"p50": float(np.percentile(step1_ms, 50)), "p99": float(np.percentile(step1_ms, 99))},
+              "clocks": clk1.summary()}
 
     e2e_val, h2d, d2h = None, 0, 0
     if not args.device_only:
-        # end to end through the C ABI from pinned host buffers.  Two handles on
-        # two streams, as a serving loop would run them: the host-to-device copy
-        # (and packing) of batch k+1 is enqueued before the solve of batch k, so
-        # it overlaps that solve.  Every step still copies all of its inputs in
-        # and its results out inside the timed region.
+        # end to end through the C ABI from pinned host buffers, on the same
+        # INFLIGHT handles and streams: the host-to-device copy (and packing)
+        # of batch k+1 is enqueued before the solve of batch k, so it overlaps
+        # that solve.  Every step still copies all of its inputs in and its
+        # results out inside the timed region.
         h_in = pinmpc.device_inputs(batch, pin_host=True)
-        solvers = [solver, pinmpc.solver_for(batch, max_iter=args.max_iter)]
-        streams = [stream, torch.cuda.Stream(dev)]
 
         def pinned_outputs():
             return (torch.empty((B, N, 13), dtype=torch.float32).pin_memory(),
@@ -358,7 +393,7 @@ def run_gpu(args):
                     torch.empty(B, dtype=torch.int32).pin_memory(),
                     torch.empty(B, dtype=torch.float32).pin_memory())
 
-        outs = [pinned_outputs(), pinned_outputs()]
+        outs = [pinned_outputs() for _ in range(INFLIGHT)]
         h2d = sum(v.numel() * v.element_size() for v in h_in.values())
         d2h = sum(v.numel() * v.element_size() for v in outs[0])
 
@@ -366,8 +401,8 @@ def run_gpu(args):
             solvers[0].set_stages(B, N, **h_in, stream=streams[0])
             for k in range(K):
                 if k + 1 < K:
-                    solvers[(k + 1) % 2].set_stages(B, N, **h_in, stream=streams[(k + 1) % 2])
-                sl = k % 2
+                    solvers[(k + 1) % INFLIGHT].set_stages(B, N, **h_in, stream=streams[(k + 1) % INFLIGHT])
+                sl = k % INFLIGHT
                 solvers[sl].solve(B, stream=streams[sl])
                 o = outs[sl]
                 solvers[sl].get_traj(o[0], o[1], o[2], None, o[3], None, stream=streams[sl])
@@ -380,8 +415,8 @@ def run_gpu(args):
         e2e_run(args.steps)
         barrier()
         e2e_s = (time.perf_counter() - t0) / args.steps
-        last = outs[(args.steps - 1) % 2]
-        e2e_ok = int(((last[2].numpy() == 0) & (last[3].numpy() <= KKT_TOL)).sum())
+        last_o = outs[(args.steps - 1) % INFLIGHT]
+        e2e_ok = int(((last_o[2].numpy() == 0) & (last_o[3].numpy() <= KKT_TOL)).sum())
         e2e_s, e2e_ok = job_totals(world, e2e_s, e2e_ok, dev)
         e2e_val = e2e_ok / e2e_s
 
@@ -407,13 +442,16 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "global_batch": world * B, "horizon": N, "seed": SEED,
                    "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
+                   "inflight": INFLIGHT,
                    "max_iter": args.max_iter},
         "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
                 if e2e_val is not None else None),
+        "single_stream": single,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
                      "kernel": dom, "ms_per_launch": kernels[dom]["ms_per_launch"],
+                     "timing": "per-launch CUDA events over the single_stream timed steps (no overlapping launches)",
                      "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived; no FP32 peak is measured)",
                      "kernels": kernels, "solve_ms": solve_avg, "pack_ms": statistics.mean(pack_ms), "src": h},
         "clocks": clk.summary(),
@@ -425,7 +463,8 @@ def run_gpu(args):
     }
     # served latency of a batch: set_stages -> get_traj complete, per timed step
     line["latency_ms"] = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                          "what": f"one batch of {B} solves, set_stages to get_traj complete (device events)"}
+                          "what": f"one batch of {B} solves, set_stages to get_traj complete (device events), "
+                                  f"{INFLIGHT} batches in flight (single_stream.latency_ms: one in flight)"}
     if refs:
         # per-instance error of the last timed step against the oracle's solutions
         # of the instances the CPU baseline leg solved (same workload, same seed)
