@@ -382,9 +382,8 @@ def run_gpu(args):
     if not args.device_only:
         # end to end through the C ABI from pinned host buffers, on the same
         # INFLIGHT handles and streams: the host-to-device copy (and packing)
-        # of batch k+1 is enqueued before the solve of batch k, so it overlaps
-        # that solve.  Every step still copies all of its inputs in and its
-        # results out inside the timed region.
+        # of batch k+1 overlaps the solve of batch k.  Every step copies all
+        # of its inputs in and its results out inside the timed region.
         h_in = pinmpc.device_inputs(batch, pin_host=True)
 
         def pinned_outputs():
@@ -398,11 +397,13 @@ def run_gpu(args):
         d2h = sum(v.numel() * v.element_size() for v in outs[0])
 
         def e2e_run(K):
-            solvers[0].set_stages(B, N, **h_in, stream=streams[0])
+            # nothing here blocks the host (pinned buffers make get_traj
+            # asynchronous): step k's copies and kernels queue on its handle's
+            # stream behind step k - INFLIGHT, and the host reads the results
+            # once every stream has drained
             for k in range(K):
-                if k + 1 < K:
-                    solvers[(k + 1) % INFLIGHT].set_stages(B, N, **h_in, stream=streams[(k + 1) % INFLIGHT])
                 sl = k % INFLIGHT
+                solvers[sl].set_stages(B, N, **h_in, stream=streams[sl])
                 solvers[sl].solve(B, stream=streams[sl])
                 o = outs[sl]
                 solvers[sl].get_traj(o[0], o[1], o[2], None, o[3], None, stream=streams[sl])

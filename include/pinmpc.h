@@ -159,14 +159,17 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream);
  *                           F = 2*(contact_dim==3 ? 2 : 5) + 2 faces per contact
  *                           ordered (+t_1, -t_1, +t_2, -t_2, ..., -n <= 0, n <= n_max);
  *                           a face is active when g_f(u) >= -1e-5 (1 + n_max)
- * Stages at or beyond an instance's horizon are written as 0.  With host
- * pointers this call synchronizes `stream`. */
+ * Stages at or beyond an instance's horizon are written as 0.  Device or
+ * host pointers: with pageable host memory this call synchronizes `stream`;
+ * with device or page-locked (pinned) memory it is asynchronous, and the
+ * results are there once `stream` has passed this call. */
 mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status,
                         int32_t* iters, float* kkt, uint64_t* active_bits, void* stream);
 
 /* Per-instance solver statistics of the last solve: polishes [B] = number
  * of active-set polish attempts (Riccati scans) the instance ran.  Device
- * or host pointer; host pointers synchronize `stream`. */
+ * or host pointer; pageable host memory synchronizes `stream` (see
+ * mpc_get_traj). */
 mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream);
 
 /* Receding-horizon warm start: the next mpc_solve_batch starts instances
@@ -186,7 +189,7 @@ mpc_status mpc_warm_start(mpc_handle* h, int32_t shift, void* stream);
  * summed over its Riccati scans, the number of free input components of
  * every stage (the elimination steps actually run).  A work count for
  * throughput accounting; no counterpart in the paper.  Device or host
- * pointer; host pointers synchronize `stream`. */
+ * pointer; pageable host memory synchronizes `stream` (see mpc_get_traj). */
 mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream);
 
 /* Per-kernel device timing (no counterpart in the paper; off by default).

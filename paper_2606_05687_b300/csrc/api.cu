@@ -164,6 +164,12 @@ struct mpc_handle {
     int warm_B = 0, warm_N = 0;  // a warm start is pending for instances [0, warm_B) at horizon stride warm_N
     float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
     float* staging = nullptr;  // device copies of host-memory inputs
+    // host-input copies run on their own stream: they wait only until the
+    // previous pack has read the staging buffer, so they overlap the solve
+    // queued before them on the caller's stream
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t staged = nullptr, consumed = nullptr;
+    bool consumed_valid = false;
     size_t staging_floats = 0;
     uint64_t bytes = 0;
     int B_set = 0, N_set = 0;
@@ -272,6 +278,18 @@ static bool is_host_pointer(const void* p) {
         return true;
     }
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// Host memory the CUDA runtime does not know (not page-locked): a copy into
+// it is complete only once the stream has reached it.
+static bool is_pageable_pointer(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeUnregistered;
 }
 
 extern "C" {
@@ -448,12 +466,22 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
             h->staging_floats = need;
             h->bytes += need * 4;
         }
+        if (!h->copy_stream) {
+            if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->staged, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->consumed, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, MPC_ERR_CUDA, "copy stream or event creation failed");
+            }
+        }
+        if (h->consumed_valid && (e = cudaStreamWaitEvent(h->copy_stream, h->consumed, 0)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaStreamWaitEvent");
         size_t off = 0;
         for (int i = 0; i < 13; ++i) {
             if (!src[i]) { dev[i] = nullptr; continue; }
             if (is_host_pointer(src[i])) {
                 float* d = h->staging + off;
-                if ((e = cudaMemcpyAsync(d, src[i], cnt[i] * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                if ((e = cudaMemcpyAsync(d, src[i], cnt[i] * 4, cudaMemcpyHostToDevice, h->copy_stream)) != cudaSuccess)
                     return cuda_fail(h, e, "cudaMemcpyAsync (stage data)");
                 dev[i] = d;
             } else {
@@ -461,6 +489,9 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
             }
             off += (cnt[i] + 63) & ~size_t(63);
         }
+        if ((e = cudaEventRecord(h->staged, h->copy_stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, h->staged, 0)) != cudaSuccess)
+            return cuda_fail(h, e, "staging event");
     } else {
         for (int i = 0; i < 13; ++i) dev[i] = src[i];
     }
@@ -477,6 +508,10 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     a.rec = h->rec;
     if ((e = timed_launch(h, kClassPack, s, [&] { h->shape.launch_pack(a, (int)B, s); })) != cudaSuccess)
         return cuda_fail(h, e, "pack kernel launch");
+    if (any_host) {
+        if ((e = cudaEventRecord(h->consumed, s)) != cudaSuccess) return cuda_fail(h, e, "staging event");
+        h->consumed_valid = true;
+    }
     h->B_set = (int)B;
     h->N_set = (int)N;
     h->have_stages = true;
@@ -575,7 +610,7 @@ mpc_status mpc_get_traj(mpc_handle* h, float* xi, float* u, int32_t* status, int
     bool host = false;
     for (auto& x : cp) {
         if (!x.dst) continue;
-        host |= is_host_pointer(x.dst);
+        host |= is_pageable_pointer(x.dst);
         if ((e = cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDefault, s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemcpyAsync (results)");
     }
@@ -592,7 +627,7 @@ mpc_status mpc_get_stats(mpc_handle* h, int32_t* polishes, void* stream) {
     if (polishes) {
         if ((e = cudaMemcpyAsync(polishes, h->out_npol, (size_t)h->B_solved * 4, cudaMemcpyDefault, s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemcpyAsync (stats)");
-        if (is_host_pointer(polishes) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        if (is_pageable_pointer(polishes) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaStreamSynchronize");
     }
     return MPC_OK;
@@ -607,7 +642,7 @@ mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream) {
     if (pivots) {
         if ((e = cudaMemcpyAsync(pivots, h->out_piv, (size_t)h->B_solved * 4, cudaMemcpyDefault, s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemcpyAsync (pivots)");
-        if (is_host_pointer(pivots) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        if (is_pageable_pointer(pivots) && (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(h, e, "cudaStreamSynchronize");
     }
     return MPC_OK;
@@ -660,6 +695,9 @@ void mpc_destroy(mpc_handle* h) {
         cudaEventDestroy(t.stop);
     }
     for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->staged) cudaEventDestroy(h->staged);
+    if (h->consumed) cudaEventDestroy(h->consumed);
     cudaFree(h->out_piv);
     cudaFree(h->rec);
     cudaFree(h->out_xi);

@@ -129,10 +129,17 @@ def test_host_buffers_match_device_buffers(pinmpc):
     xi = np.empty((batch.B, batch.N, 13), np.float32)
     u = np.empty((batch.B, batch.N, batch.nu), np.float32)
     st = np.empty(batch.B, np.int32)
-    s.get_traj(xi=xi, u=u, status=st)
-    torch.cuda.synchronize()
+    s.get_traj(xi=xi, u=u, status=st)  # pageable memory: synchronous
     assert np.array_equal(xi, dev["xi"]) and np.array_equal(u, dev["u"])
     assert np.array_equal(st, dev["status"])
+    # pinned memory: asynchronous, the results are there once the stream has passed the call
+    pu = torch.empty((batch.B, batch.N, batch.nu), dtype=torch.float32).pin_memory()
+    pst = torch.full((batch.B,), -7, dtype=torch.int32).pin_memory()
+    s.set_stages(batch.B, batch.N, **host)
+    s.solve(batch.B)
+    s.get_traj(u=pu, status=pst)
+    torch.cuda.current_stream().synchronize()
+    assert np.array_equal(pu.numpy(), dev["u"]) and np.array_equal(pst.numpy(), dev["status"])
 
 
 def test_alone_equals_in_batch_and_repeatable(pinmpc):
