@@ -15,6 +15,7 @@
 // other stages read.
 #pragma once
 #include "polish.cuh"
+#include "tma.cuh"
 
 namespace pinmpc {
 
@@ -22,8 +23,10 @@ template <class D>
 struct RoundSmem {
     static constexpr int kTmp = 5;  // per-warp scratch vectors
     static constexpr int FR = 16;   // padded row length of S_j and W_j
-    int sd, var, xb, tmp, pre, fac, part, total;
-    __host__ __device__ explicit RoundSmem(int N) {
+    int sd, var, xb, tmp, pre, fac, part, sd2, fac2, total;
+    // dbl: a second record and factor buffer, which TMA fills for the next
+    // instance while the current one iterates
+    __host__ __device__ explicit RoundSmem(int N, bool dbl = false) {
         int o = 0;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
         sd = take(N * D::SREC);
@@ -33,6 +36,8 @@ struct RoundSmem {
         pre = take(N * 3 * D::NBP);
         fac = take(N * 2 * D::NX * FR);
         part = take(32);
+        sd2 = dbl ? take(N * D::SREC) : sd;
+        fac2 = dbl ? take(N * 2 * D::NX * FR) : fac;
         total = o;
     }
     __host__ __device__ int bytes() const { return total * 4; }
@@ -507,11 +512,11 @@ __device__ void round_fail(const RoundArgs& a, int b, int status) {
 // One round of ADMM iterations (a.m0, a.m1] for one instance per CTA; the
 // factor cache and the iterate stay in global memory between rounds.
 template <class D, int MAXT>
-__device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float* smem) {
+__device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float* smem, int buf) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     constexpr bool TWO = RegT<D>::kTwo;
     if (a.done[b]) return;
-    const RoundSmem<D> L(a.N);
+    const RoundSmem<D> L(a.N, a.dbl != 0);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const float* rec = a.rec + (size_t)b * a.irec;
     const float* tail = rec + (size_t)a.n_rec * D::SREC;
@@ -530,10 +535,10 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     }
     RCtx<D> c;
     c.var = smem + L.var; c.xb = smem + L.xb; c.tmp = smem + L.tmp; c.pre = smem + L.pre;
-    c.fac = smem + L.fac; c.part = smem + L.part;
+    c.fac = smem + (buf ? L.fac2 : L.fac); c.part = smem + L.part;
     c.N = a.N; c.Nh = Nh; c.rho = a.rho;
-    float* sd = smem + L.sd;
-    {
+    float* sd = smem + (buf ? L.sd2 : L.sd);
+    if (!a.dbl) {  // otherwise the records are already there (TMA)
         const float4* src = reinterpret_cast<const float4*>(rec);
         float4* dst = reinterpret_cast<float4*>(sd);
         const int n4 = Nh * D::SREC / 4;
@@ -568,7 +573,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         c.pre[(k * 3 + PIDN) * NBP + i] = idn;
     }
     __syncthreads();
-    {
+    if (!a.dbl) {
         const float4* fs = reinterpret_cast<const float4*>(gcache);
         float4* fd = reinterpret_cast<float4*>(c.fac);
         for (int e = tid; e < Nh * 2 * NX * FR / 4; e += nthr) fd[e] = fs[e];
@@ -723,14 +728,53 @@ __global__ void warm_shift_kernel(float* state, const float* rec, int irec, int 
 
 // One round of ADMM iterations (a.m0, a.m1]: persistent CTAs (one per SM), each
 // taking instances of the round's list until it is exhausted.
+// Thread 0: start the TMA copies of instance b's records (the first a.N
+// stages) and factors into buffer buf, completing on bar[buf].
+template <class D>
+__device__ __noinline__ void round_fetch(const RoundArgs& a, float* smem, uint64_t* bar, int b, int buf) {
+    const RoundSmem<D> L(a.N, true);
+    const uint32_t rec_bytes = (uint32_t)(a.N * D::SREC * sizeof(float));
+    const uint32_t fac_bytes = (uint32_t)(RoundSmem<D>::cache_floats(a.N) * sizeof(float));
+    mbar_arrive_expect_tx(&bar[buf], rec_bytes + fac_bytes);
+    bulk_copy_g2s(smem + (buf ? L.sd2 : L.sd), a.rec + (size_t)b * a.irec, rec_bytes, &bar[buf]);
+    bulk_copy_g2s(smem + (buf ? L.fac2 : L.fac), a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N), fac_bytes,
+                  &bar[buf]);
+}
+
+// With a.dbl, thread 0 starts the TMA copies of the next instance's records
+// and factors into the other buffer as soon as it knows that instance, so
+// they arrive while the current instance iterates.
 template <class D, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int item;
-    for (;;) {
-        const int b = next_instance(a, 0, &item);
-        if (b < 0) break;
-        round_instance<D, MAXT>(a, b, smem);
+    __shared__ __align__(8) uint64_t bar[2];
+    const bool dbl = a.dbl != 0;
+    if (dbl && threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    int b = next_instance(a, 0, &item);  // starts with a barrier: the initialisation is visible
+    if (b < 0) return;
+    if (dbl && threadIdx.x == 0) round_fetch<D>(a, smem, bar, b, 0);
+    for (int it = 0;; ++it) {
+        // buffers alternate, so buffer it & 1 completes its (it >> 1)-th phase now
+        const int cur = dbl ? (it & 1) : 0;
+        const int bn = next_instance(a, 0, &item);
+        if (dbl) {
+            if (bn >= 0 && threadIdx.x == 0) round_fetch<D>(a, smem, bar, bn, cur ^ 1);
+            const bool ok = __syncthreads_and(mbar_wait(&bar[cur], (uint32_t)(it >> 1) & 1u));
+            if (!ok) {
+                // the copies did not arrive: report this instance, let the other
+                // buffer's copies land (bounded), and stop taking work
+                if (bn >= 0) mbar_wait(&bar[cur ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+                round_fail<D>(a, b, kTimeout);
+                return;
+            }
+        }
+        round_instance<D, MAXT>(a, b, smem, cur);
+        if (bn < 0) break;
+        b = bn;
     }
 }
 

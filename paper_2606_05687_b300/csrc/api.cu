@@ -34,7 +34,7 @@ struct Shape {
     cudaError_t (*set_round_attrs)(int round_bytes, int polish_bytes);
     void (*launch_round)(const RoundArgs&, int B, int smem, cudaStream_t);
     void (*launch_polish)(const RoundArgs&, int B, int smem, cudaStream_t);
-    int (*round_smem)(int N);
+    int (*round_smem)(int N, bool dbl);
     int (*cache_floats)(int N);
     void (*launch_factor)(const FactorArgs&, cudaStream_t);
     int (*resident_per_sm)(int kernel, int N, int smem);  // kernel 0 round, 1 polish
@@ -60,7 +60,7 @@ int polish_smem_t(int N) { return CtaSmem<D>(N).total * 4; }
 template <class D>
 int state_floats_t(int N) { return RoundState<D>::floats(N); }
 template <class D>
-int round_smem_t(int N) { return RoundSmem<D>(N).bytes(); }
+int round_smem_t(int N, bool dbl) { return RoundSmem<D>(N, dbl).bytes(); }
 template <class D>
 int cache_floats_t(int N) { return RoundSmem<D>::cache_floats(N); }
 template <class D>
@@ -161,6 +161,8 @@ struct mpc_handle {
     int* lists = nullptr;        // [2][B_max] instances still running, by round parity
     int* work = nullptr;         // [4] round cursor, polish cursor, list counts [2]
     int sms = 0;                 // streaming multiprocessors of the device
+    int optin_smem = 0;          // opt-in shared memory per CTA
+    int round_attr = 0;          // dynamic shared memory the round kernel is set up for
     int warm_B = 0, warm_N = 0;  // a warm start is pending for instances [0, warm_B) at horizon stride warm_N
     float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
     float* staging = nullptr;  // device copies of host-memory inputs
@@ -369,10 +371,10 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     if (sh.polish_smem(c.N_max) > max_optin_smem(c.device))
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: polish needs %d B shared memory", c.N_max,
                     sh.polish_smem(c.N_max));
-    if (sh.round_smem(c.N_max) > max_optin_smem(c.device))
+    if (sh.round_smem(c.N_max, false) > max_optin_smem(c.device))
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: ADMM rounds need %d B shared memory", c.N_max,
-                    sh.round_smem(c.N_max));
-    if ((e = sh.set_round_attrs(sh.round_smem(c.N_max), sh.polish_smem(c.N_max))) != cudaSuccess)
+                    sh.round_smem(c.N_max, false));
+    if ((e = sh.set_round_attrs(sh.round_smem(c.N_max, false), sh.polish_smem(c.N_max))) != cudaSuccess)
         return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
 
     mpc_handle* h = new (std::nothrow) mpc_handle();
@@ -382,6 +384,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
         cudaGetLastError();
         h->sms = 1;
     }
+    h->optin_smem = max_optin_smem(c.device);
+    h->round_attr = sh.round_smem(c.N_max, false);
     h->shape = sh;
     h->nc = c.n_contacts;
     h->nu = c.n_contacts * c.contact_dim;
@@ -537,7 +541,16 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
-    const int round_smem = h->shape.round_smem(h->N_set);
+    // double-buffered records and factors (TMA prefetch) when they fit
+    const int smem_single = h->shape.round_smem(h->N_set, false), smem_dbl = h->shape.round_smem(h->N_set, true);
+    const bool dbl = smem_dbl <= h->optin_smem;
+    const int round_smem = dbl ? smem_dbl : smem_single;
+    if (round_smem > h->round_attr) {
+        if ((e = h->shape.set_round_attrs(round_smem, h->shape.polish_smem(c.N_max))) != cudaSuccess)
+            return cuda_fail(h, e, "cudaFuncSetAttribute");
+        h->round_attr = round_smem;
+    }
+    r.dbl = dbl ? 1 : 0;
     const int polish_smem = h->shape.polish_smem(h->N_set);
     if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");

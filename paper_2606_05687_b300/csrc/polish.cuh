@@ -41,6 +41,7 @@ struct RoundArgs {
     int* cnt_out;
     int* cursor;             // [2] work cursors of the round and polish kernels, zeroed per round
     int warm_B;              // instances b < warm_B start round 0 from the stored (shifted) iterate
+    int dbl;                 // round kernel: records and factors arrive by TMA into two alternating buffers
     float* Kst;              // [B][N][NU][NX+1] polish gains
     float* out_xi;
     float* out_u;
