@@ -42,9 +42,9 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # keyed "class:source hash"; a changed source makes the entry stale (null)
 MEASURED_TRAFFIC = {
     # profiles/polish_cta_kernel_walking_B4096_N20.md: round-0 launch (all 4096 instances)
-    "polish:3cfe95b24a0fd308": 293040128,
+    "polish:b5edbdcc7238c133": 292693248,
     # profiles/round2_kernel_walking_B4096_N20.md: round-0 launch
-    "round:3cfe95b24a0fd308": 443067648,
+    "round:b5edbdcc7238c133": 440435968,
 }
 
 
