@@ -451,6 +451,7 @@ def run_gpu(args):
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
+                     "traffic_note": "dram bytes read + written by the round-0 launch (all instances), one ncu capture",
                      "kernel": dom, "ms_per_launch": kernels[dom]["ms_per_launch"],
                      "timing": "per-launch CUDA events over the single_stream timed steps (no overlapping launches)",
                      "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived; no FP32 peak is measured)",
