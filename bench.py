@@ -421,6 +421,18 @@ def run_gpu(args):
         e2e_s, e2e_ok = job_totals(world, e2e_s, e2e_ok, dev)
         e2e_val = e2e_ok / e2e_s
 
+    served = None
+    if not args.device_only and world == 1:
+        # served latency: single-environment requests arriving as a Poisson
+        # stream at 70 % of the measured capacity for 1 s, continuously batched
+        # (up to B per batch) over two handles
+        from paper_2606_05687_b300.serve import BatchServer, poisson_arrivals, serve_load
+        srv = BatchServer(t, batch.nx, batch.nc, batch.contact_dim, B_max=B, N=N, n_handles=INFLIGHT,
+                          max_iter=args.max_iter)
+        serve_load(srv, poisson_arrivals(0.7 * value, 0.2, B, seed=SEED + 1))  # warm-up
+        served = serve_load(srv, poisson_arrivals(0.7 * value, 1.0, B, seed=SEED))
+        srv.close()
+
     if rank != 0:
         return
     # roofline of the dominant kernel from the live per-kernel times (each
@@ -448,6 +460,7 @@ def run_gpu(args):
         "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
                 if e2e_val is not None else None),
         "single_stream": single,
+        "served": served,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),

@@ -1,0 +1,185 @@
+"""Continuous batching of single-environment MPC solves over the C ABI.
+
+Requests (one environment each, with the stage data of its next MPC step)
+arrive over time and queue first-in first-out.  Whenever one of the
+server's handles is idle and requests are waiting, the dispatcher takes up
+to ``B_max`` of them, gathers their stage data into that handle's device
+input buffers (on the handle's stream), and enqueues set_stages / solve /
+get_traj there; a CUDA event marks the batch done.  Several handles keep
+several batches in flight, so a batch forms while others run.  Each
+request's latency runs from its arrival to the host observing its batch's
+event.  Requests are kept in arrays (a batch is a contiguous run of the
+queue), so the host loop costs per batch, not per request.
+
+Every instance of a batch is solved independently, so a request's result
+does not depend on which other requests share its batch (the tests check
+this bit for bit).  A batch starts every instance cold: the receding-horizon
+warm start (mpc_warm_start) keeps state per batch slot, and a continuously
+re-formed batch has no stable slots.
+"""
+from __future__ import annotations
+
+import time
+from typing import Callable, Dict, Optional
+
+import numpy as np
+
+from . import pinmpc
+
+STAGE_KEYS = ("A", "Bm", "e", "Q", "R", "ry", "ru", "mu", "fmax", "mask", "xi0", "u_prev", "horizon")
+
+
+class BatchServer:
+    """Continuous batching over ``n_handles`` solver handles.
+
+    ``pool`` holds the stage data of every environment the requests refer to
+    (torch tensors on the device, keyed like ``pinmpc.device_inputs``; row e
+    is environment e).  ``clock`` returns seconds.  Request r (in submission
+    order) has ``env[r]``, ``t_arrival[r]``, and once served ``t_done[r]``
+    and ``status[r]``.
+    """
+
+    def __init__(self, pool: Dict[str, "object"], nx: int, nc: int, contact_dim: int, B_max: int, N: int,
+                 n_handles: int = 2, clock: Callable[[], float] = time.perf_counter, **overrides):
+        import torch
+        self.torch = torch
+        self.pool = pool
+        self.B_max, self.N = B_max, N
+        self.clock = clock
+        self.device = pool["A"].device
+        self.handles = []
+        for _ in range(n_handles):
+            cfg = pinmpc.default_config(nx, nc, contact_dim, B_max, N, **overrides)
+            solver = pinmpc.Solver(cfg)
+            inputs = {k: torch.empty((B_max,) + tuple(pool[k].shape[1:]), dtype=pool[k].dtype, device=self.device)
+                      for k in STAGE_KEYS}
+            outs = dict(u=torch.empty((B_max, N, nc * contact_dim), dtype=torch.float32, device=self.device),
+                        xi=torch.empty((B_max, N, nx), dtype=torch.float32, device=self.device),
+                        status=torch.empty(B_max, dtype=torch.int32, device=self.device),
+                        kkt=torch.empty(B_max, dtype=torch.float32, device=self.device))
+            status_host = torch.empty(B_max, dtype=torch.int32).pin_memory()
+            self.handles.append(dict(solver=solver, stream=torch.cuda.Stream(self.device), inputs=inputs,
+                                     outs=outs, status_host=status_host, busy=None, event=None))
+        cap = 1 << 16
+        self.env = np.zeros(cap, np.int64)
+        self.t_arrival = np.zeros(cap)
+        self.t_done = np.full(cap, np.nan)
+        self.status = np.full(cap, -1, np.int32)
+        self.n = 0          # requests submitted
+        self.head = 0       # first request not yet dispatched
+        self.batches = 0
+        self.results: Dict[int, dict] = {}
+        self.keep_results = False
+
+    def _grow(self, need):
+        cap = len(self.env)
+        while cap < need:
+            cap *= 2
+        if cap != len(self.env):
+            for name, fill in (("env", 0), ("t_arrival", 0.0), ("t_done", np.nan), ("status", -1)):
+                a = getattr(self, name)
+                b = np.full(cap, fill, a.dtype)
+                b[:len(a)] = a
+                setattr(self, name, b)
+
+    def submit(self, envs, t_arrival: Optional[np.ndarray] = None):
+        """Queue requests for environments `envs` (arrival times default to now)."""
+        envs = np.atleast_1d(np.asarray(envs, np.int64))
+        k = len(envs)
+        self._grow(self.n + k)
+        self.env[self.n:self.n + k] = envs
+        self.t_arrival[self.n:self.n + k] = self.clock() if t_arrival is None else t_arrival
+        self.n += k
+
+    @property
+    def queued(self) -> int:
+        return self.n - self.head
+
+    def busy(self) -> bool:
+        return any(h["busy"] is not None for h in self.handles)
+
+    def _dispatch(self, h):
+        torch = self.torch
+        lo = self.head
+        hi = min(self.n, lo + self.B_max)
+        self.head = hi
+        B = hi - lo
+        with torch.cuda.stream(h["stream"]):
+            idx = torch.from_numpy(self.env[lo:hi]).to(self.device, non_blocking=True)
+            for k in STAGE_KEYS:
+                torch.index_select(self.pool[k], 0, idx, out=h["inputs"][k][:B])
+        view = {k: h["inputs"][k][:B] for k in STAGE_KEYS}
+        s = h["solver"]
+        s.set_stages(B, self.N, **view, stream=h["stream"])
+        s.solve(B, stream=h["stream"])
+        o = h["outs"]
+        s.get_traj(xi=o["xi"], u=o["u"], status=o["status"], kkt=o["kkt"], stream=h["stream"])
+        with torch.cuda.stream(h["stream"]):
+            h["status_host"][:B].copy_(o["status"][:B], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(h["stream"])
+        h["busy"], h["event"] = (lo, hi), ev
+        self.batches += 1
+
+    def _retire(self, h, now):
+        lo, hi = h["busy"]
+        self.t_done[lo:hi] = now
+        self.status[lo:hi] = h["status_host"][:hi - lo].numpy()
+        if self.keep_results:
+            o = {k: h["outs"][k][:hi - lo].cpu().numpy() for k in ("u", "xi", "kkt")}
+            for i in range(hi - lo):
+                self.results[lo + i] = {k: o[k][i] for k in o}
+        h["busy"], h["event"] = None, None
+
+    def step(self):
+        """One pass of the serving loop: retire finished batches, start new ones."""
+        now = None
+        for h in self.handles:
+            if h["busy"] is not None and h["event"].query():
+                now = self.clock() if now is None else now
+                self._retire(h, now)
+        for h in self.handles:
+            if h["busy"] is None and self.queued:
+                self._dispatch(h)
+
+    def drain(self):
+        while self.queued or self.busy():
+            self.step()
+
+    def close(self):
+        for h in self.handles:
+            h["solver"].close()
+
+
+def poisson_arrivals(rate: float, duration: float, n_env: int, seed: int = 0) -> np.ndarray:
+    """[(t, env)] with exponential inter-arrival times (rate per second) over
+    `duration` seconds, environments drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    n = int(rate * duration * 1.2) + 16
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    t = t[t < duration]
+    env = rng.integers(0, n_env, size=t.size)
+    return np.stack([t, env], axis=1)
+
+
+def serve_load(server: BatchServer, arrivals: np.ndarray) -> dict:
+    """Replay `arrivals` in real time through `server`; per-request latency
+    percentiles (ms) and the achieved throughput (requests/s)."""
+    t0 = server.clock()
+    i, n = 0, len(arrivals)
+    first, batches0 = server.n, server.batches
+    times = arrivals[:, 0]
+    while i < n or server.queued or server.busy():
+        now = server.clock() - t0
+        j = int(np.searchsorted(times, now, side="right"))
+        if j > i:
+            server.submit(arrivals[i:j, 1].astype(np.int64), t0 + times[i:j])
+            i = j
+        server.step()
+    lo, hi = first, server.n
+    lat = (server.t_done[lo:hi] - server.t_arrival[lo:hi]) * 1e3
+    span = float(np.max(server.t_done[lo:hi])) - t0
+    return {"requests": hi - lo, "certified": int(np.sum(server.status[lo:hi] == 0)),
+            "offered_per_s": (hi - lo) / max(float(times[-1]), 1e-9), "achieved_per_s": (hi - lo) / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_batch": (hi - lo) / max(server.batches - batches0, 1)}
