@@ -129,7 +129,9 @@ typedef struct mpc_handle mpc_handle;
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,
                               int32_t contact_dim, int32_t B_max, int32_t N_max);
 
-/* Largest horizon this build supports for (nx, nu); 0 if the shape is not built. */
+/* Largest horizon N_max that mpc_create accepts for (nx, nu): 32 (one warp
+ * per stage) for both built shapes; 0 if the shape is not built.
+ * mpc_solve_noalloc has a lower limit of its own for nu = 24 (below). */
 int32_t mpc_max_horizon(int32_t nx, int32_t nu);
 
 /* Validate cfg, select its device and allocate the workspace (owned by the
@@ -222,7 +224,9 @@ mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, in
  * Every call shares the one array: calls whose work overlaps on the GPU
  * (different streams, or host threads) race and must be serialized by the
  * caller.  Each call rewrites every scratch word it reads, so nothing carries
- * over from the previous call. */
+ * over from the previous call.  Its single kernel holds a whole instance in
+ * shared memory, which caps the horizon at 24 stages for nu = 24 (32 for
+ * nu = 12); a longer one is rejected with MPC_ERR_UNSUPPORTED. */
 mpc_status mpc_solve_noalloc(const mpc_config* cfg, const mpc_stage_view* v, float* xi, float* u,
                              int32_t* status, int32_t* iters, float* kkt, void* stream);
 

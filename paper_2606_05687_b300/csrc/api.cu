@@ -25,10 +25,7 @@ thread_local std::string g_create_error;
 
 struct Shape {
     int srec, tail;
-    int (*smem_bytes)(int N);
-    cudaError_t (*set_smem_attr)(int bytes);
     void (*launch_pack)(const PackArgs&, int B, cudaStream_t);
-    void (*launch_solve)(const SolveArgs&, int B, int n_rec, int smem, cudaStream_t);
     int (*polish_smem)(int N);
     int (*state_floats)(int N);
     cudaError_t (*set_round_attrs)(int round_bytes, int polish_bytes);
@@ -44,17 +41,7 @@ struct Shape {
 };
 
 template <class D>
-int smem_bytes_t(int N) { return Smem<D>(N).bytes(); }
-template <class D>
-cudaError_t set_smem_attr_t(int bytes) {
-    return cudaFuncSetAttribute(solve_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-template <class D>
 void launch_pack_t(const PackArgs& a, int B, cudaStream_t s) { pack_kernel<D><<<B, 256, 0, s>>>(a); }
-template <class D>
-void launch_solve_t(const SolveArgs& a, int B, int n_rec, int smem, cudaStream_t s) {
-    solve_kernel<D><<<B, 32 * a.N, smem, s>>>(a, n_rec);
-}
 template <class D>
 int polish_smem_t(int N) { return CtaSmem<D>(N).total * 4; }
 template <class D>
@@ -112,8 +99,7 @@ cudaError_t set_warm_attr_t(int bytes) {
 }
 template <class D>
 Shape make_shape() {
-    return Shape{D::SREC,         D::TAIL,           smem_bytes_t<D>,      set_smem_attr_t<D>,
-                 launch_pack_t<D>, launch_solve_t<D>, polish_smem_t<D>,     state_floats_t<D>,
+    return Shape{D::SREC,         D::TAIL,           launch_pack_t<D>,     polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
                  cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>, launch_warm_shift_t<D>,
                  set_warm_attr_t<D>};
@@ -328,9 +314,10 @@ int32_t mpc_max_horizon(int32_t nx, int32_t nu) {
     Shape sh;
     const int cd = (nu == 24) ? 3 : 6;
     if (nu % cd != 0 || !pick_shape(nx, nu / cd, cd, &sh)) return 0;
+    // one warp per stage (32 stages at most) and each kernel's shared memory
     int best = 0;
     for (int N = 1; N <= 32; ++N)
-        if (sh.smem_bytes(N) <= kSmemLimit) best = N;
+        if (sh.round_smem(N, false) <= kSmemLimit && sh.polish_smem(N) <= kSmemLimit) best = N;
     return best;
 }
 
@@ -362,12 +349,6 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     }
     if (c.device < 0 || c.device >= ndev) return fail(nullptr, MPC_ERR_INVALID_ARG, "bad device ordinal %d", c.device);
     if ((e = cudaSetDevice(c.device)) != cudaSuccess) return fail(nullptr, MPC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-    const int smem = sh.smem_bytes(c.N_max);
-    if (smem > max_optin_smem(c.device))
-        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d needs %d B shared memory per CTA (limit %d)", c.N_max,
-                    smem, max_optin_smem(c.device));
-    if ((e = sh.set_smem_attr(smem)) != cudaSuccess)
-        return fail(nullptr, MPC_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     if (sh.polish_smem(c.N_max) > max_optin_smem(c.device))
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d: polish needs %d B shared memory", c.N_max,
                     sh.polish_smem(c.N_max));

@@ -60,8 +60,8 @@ def test_defaults_and_limits(P):
     assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(2e-6)
     assert cfg.polish == 1 and cfg.accel == 1
     lib = P.load()
-    assert lib.mpc_max_horizon(13, 24) >= 20
-    assert lib.mpc_max_horizon(13, 12) >= 20
+    assert lib.mpc_max_horizon(13, 24) == 32  # one warp per stage
+    assert lib.mpc_max_horizon(13, 12) == 32
     assert lib.mpc_max_horizon(13, 7) == 0
 
 

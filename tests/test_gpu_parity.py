@@ -165,3 +165,24 @@ def test_plain_admm_certificate_is_honest(pinmpc):
         rep = okkt.kkt_residual(inst, out["xi"][b].astype(np.float64), out["u"][b].astype(np.float64))
         assert abs(out["kkt"][b] - rep.kkt) <= 0.2 * rep.kkt + 5e-7, (b, out["kkt"][b], rep.kkt)
         assert out["status"][b] in (0, 1)
+
+
+def test_maximum_horizon_both_contact_models(pinmpc):
+    """N = 32 (one warp per stage, the 1024-thread round kernel; records too
+    large for the double-buffered TMA prefetch) for point contacts and wrenches."""
+    assert pinmpc.load().mpc_max_horizon(13, 24) >= 32 and pinmpc.load().mpc_max_horizon(13, 12) >= 32
+    for spec in (W.rl_scale_walking(B=24, N=32, seed=31), W.small_centroidal(B=24, N=32, seed=32)):
+        batch = W.generate(spec)
+        out = pinmpc.solve_workload(batch)
+        assert np.all(out["status"] == 0), out["status"]
+        compare(batch, out, [0, 5, 11, 23])
+
+
+def test_large_batch_work_lists(pinmpc):
+    """B = 16384: persistent round CTAs and list-indexed polish CTAs over four
+    times the benchmark's batch; every instance certified, samples vs the oracle."""
+    batch = W.generate(W.rl_scale_walking(B=16384, N=20, seed=33))
+    out = pinmpc.solve_workload(batch)
+    assert np.all(out["status"] == 0) and out["kkt"].max() <= KKT_TOL
+    assert dynamics_residual(batch, out) <= 1e-6
+    compare(batch, out, [0, 4095, 4096, 9999, 16383])
