@@ -12,6 +12,7 @@
 #include "../../include/pinmpc.h"
 #include "admm.cuh"
 #include "polish_cta.cuh"
+#include "internal.h"
 
 using namespace pinmpc;
 
@@ -243,6 +244,18 @@ cudaError_t timed_launch(mpc_handle* h, int cls, cudaStream_t s, F&& launch) {
 }
 
 }  // namespace
+
+namespace pinmpc {
+bool solution_trajectory(const mpc_handle* h, const float** xi, int* B, int* N, int* nx, int* device) {
+    if (!h || !h->have_solution) return false;
+    *xi = h->out_xi;  // [B_solved][N_set][nx]
+    *B = h->B_solved;
+    *N = h->N_set;
+    *nx = h->cfg.nx;
+    *device = h->cfg.device;
+    return true;
+}
+}  // namespace pinmpc
 
 static mpc_status fail(mpc_handle* h, mpc_status st, const char* fmt, ...) {
     char buf[512];
