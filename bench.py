@@ -435,6 +435,37 @@ def run_gpu(args):
         served = serve_load(srv, poisson_arrivals(0.7 * value, 1.0, B, seed=SEED))
         srv.close()
 
+    landmark = None
+    if not args.device_only:
+        # landmark epilogue (Sec. II-C) on the last solve of handle 0: store the
+        # landmarks of every environment and evaluate the guidance reward,
+        # each timed per call with CUDA events on the handle's stream
+        from paper_2606_05687_b300 import landmarks as LMK
+        lmo = LMK.Landmarks(LMK.default_config(B, N, 13))
+        q_now = torch.zeros((B, 3), device=dev)
+        rew = torch.empty(B, device=dev)
+        cnt = torch.empty(B, dtype=torch.int32, device=dev)
+        s0 = streams[0]
+        for k in range(5):
+            lmo.store_solution(solvers[0], k, stream=s0)
+            lmo.reward(k, q_now, rew, B, count=cnt, stream=s0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = 100
+        ev[0].record(s0)
+        for k in range(reps):
+            lmo.store_solution(solvers[0], 100 + k, stream=s0)
+        ev[1].record(s0)
+        for k in range(reps):
+            lmo.reward(100 + k, q_now, rew, B, count=cnt, stream=s0)
+        ev[2].record(s0)
+        s0.synchronize()
+        store_us = ev[0].elapsed_time(ev[1]) / reps * 1e3
+        reward_us = ev[1].elapsed_time(ev[2]) / reps * 1e3
+        landmark = {"envs": B, "n_landmarks": 5, "store_us": store_us, "reward_us": reward_us,
+                    "what": "mpc_landmark_store_solution and mpc_landmark_reward per call (CUDA events, "
+                            f"{reps} calls each), the landmark epilogue of Sec. II-C"}
+        lmo.close()
+
     if rank != 0:
         return
     # roofline of the dominant kernel from the live per-kernel times (each
@@ -463,6 +494,7 @@ def run_gpu(args):
                 if e2e_val is not None else None),
         "single_stream": single,
         "served": served,
+        "landmarks": landmark,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),

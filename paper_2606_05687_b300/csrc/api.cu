@@ -21,6 +21,9 @@ namespace {
 // Shapes this build is compiled for: (nx, nu, contact_dim).
 using D24 = Dims<13, 24, 3>;  // 8 point contacts (4 corners per foot)
 using D12 = Dims<13, 12, 6>;  // 2 foot wrenches
+// the 9-state centroidal model xi = [c, l_G, k_G] with the same contact models
+using C24 = Dims<9, 24, 3>;
+using C12 = Dims<9, 12, 6>;
 
 thread_local std::string g_create_error;
 
@@ -109,6 +112,8 @@ Shape make_shape() {
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
     if (nx == 13 && cd == 3 && nc == 8) { *out = make_shape<D24>(); return true; }
     if (nx == 13 && cd == 6 && nc == 2) { *out = make_shape<D12>(); return true; }
+    if (nx == 9 && cd == 3 && nc == 8) { *out = make_shape<C24>(); return true; }
+    if (nx == 9 && cd == 6 && nc == 2) { *out = make_shape<C12>(); return true; }
     return false;
 }
 
@@ -344,7 +349,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
         return fail(nullptr, MPC_ERR_INVALID_ARG, "contact_dim must be 3 or 6 (got %d)", c.contact_dim);
     if (!pick_shape(c.nx, c.n_contacts, c.contact_dim, &sh))
         return fail(nullptr, MPC_ERR_UNSUPPORTED,
-                    "shape nx=%d n_contacts=%d contact_dim=%d not built (built: 13/8/3, 13/2/6)", c.nx,
+                    "shape nx=%d n_contacts=%d contact_dim=%d not built (built: nx 13 or 9 with 8/3 or 2/6)", c.nx,
                     c.n_contacts, c.contact_dim);
     if (c.B_max < 1 || c.N_max < 1) return fail(nullptr, MPC_ERR_INVALID_ARG, "B_max and N_max must be >= 1");
     if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||

@@ -18,6 +18,11 @@ A_k = I + dt*A_c(psi_k), B_k = dt*B_c(k), e_k = 0 (+ an optional small
 linearisation offset used by tests).  The gravity state x_13 = 9.81 is
 constant (its A row is a unit row and its B row is zero).
 
+A second model (spec.model = "cd9") is the paper's own 9-state centroidal
+model xi = [c, l_G, k_G] of Sec. II-A, linearised about a nominal CoM path
+and gravity-compensating forces (see _centroidal9); contact sets, schedules,
+input costs and draws are shared with the 13-state model.
+
 Every random number of instance b is drawn from its own generator seeded by
 (seed, b), so any subset of a batch can be regenerated without the rest.
 All returned arrays are float32 (the values both solvers consume; the oracle
@@ -55,6 +60,7 @@ class WorkloadSpec:
     e_scale: float = 0.0          # std of an optional linearisation offset e_k
     u_prev_scale: float = 0.0     # std of u_{-1} (the velocity-form initial input)
     ref_noise: float = 0.1        # std of the reference / initial-state noise
+    model: str = "srb13"          # "srb13": 13-state convex model; "cd9": the 9-state centroidal model
 
     @property
     def nu(self) -> int:
@@ -74,6 +80,17 @@ def rl_scale_walking(B: int = 4096, N: int = 20, seed: int = 1002, **kw) -> Work
     return WorkloadSpec(B=B, N=N, contact_dim=3, n_contacts=8, seed=seed,
                         schedule=kw.pop("schedule", "walking"),
                         f_max=kw.pop("f_max", 375.0), **kw)
+
+
+def centroidal9_walking(B: int = 4096, N: int = 20, seed: int = 1004, **kw) -> WorkloadSpec:
+    """The walking workload on the 9-state centroidal model of Sec. II-A
+    (eight 3-D contact points, nu = 24)."""
+    return rl_scale_walking(B=B, N=N, seed=seed, model="cd9", **kw)
+
+
+def centroidal9_small(B: int = 64, N: int = 10, seed: int = 1005, **kw) -> WorkloadSpec:
+    """Two feet with 6-D wrenches on the 9-state centroidal model."""
+    return small_centroidal(B=B, N=N, seed=seed, model="cd9", **kw)
 
 
 @dataclasses.dataclass
@@ -297,12 +314,111 @@ def generate(spec: WorkloadSpec, instances: Optional[Sequence[int]] = None) -> B
     mask = (contact_stance.astype(np.uint32)
             << np.arange(spec.n_contacts, dtype=np.uint32)).sum(-1).astype(np.uint32)
 
+    nominal = None
+    if spec.model == "cd9":
+        A, Bm, e, Q, ry, xi0, nominal = _centroidal9(spec, stack, psi, contact_stance, nb, N, dt)
+    elif spec.model != "srb13":
+        raise ValueError(f"unknown model {spec.model!r}")
+
     f32 = lambda x: np.ascontiguousarray(x, dtype=np.float32)
-    return Batch(spec=dataclasses.replace(spec, B=nb), A=f32(A), Bm=f32(Bm), e=f32(e),
-                 Q=f32(Q), R=f32(R), ry=f32(ry), ru=f32(ru), mu=f32(mu), fmax=f32(fmax),
-                 mask=mask, xi0=f32(xi0), u_prev=f32(u_prev),
-                 horizon=np.full(nb, N, dtype=np.int32),
-                 nu_arr=np.full(nb, nu, dtype=np.int32))
+    out = Batch(spec=dataclasses.replace(spec, B=nb), A=f32(A), Bm=f32(Bm), e=f32(e),
+                Q=f32(Q), R=f32(R), ry=f32(ry), ru=f32(ru), mu=f32(mu), fmax=f32(fmax),
+                mask=mask, xi0=f32(xi0), u_prev=f32(u_prev),
+                horizon=np.full(nb, N, dtype=np.int32),
+                nu_arr=np.full(nb, nu, dtype=np.int32))
+    if nominal is not None:
+        out.nominal = nominal  # linearisation point of the cd9 model (float64), for checks
+    return out
+
+
+NX9 = 9
+
+
+def _centroidal9(spec, stack, psi, contact_stance, nb, N, dt):
+    """Stage data of the 9-state centroidal model xi = [c, l_G, k_G] (Sec. II-A):
+        c+   = c + dt l_G / m
+        l_G+ = l_G + dt (m g + sum_i f_i)
+        k_G+ = k_G + dt sum_i ((p_i - c) x f_i + tau_i)
+    linearised for the LTV standard form at the nominal CoM cbar_k (moving at
+    the commanded velocity) and nominal forces fbar_i (gravity compensation
+    shared evenly by the stance contacts):
+        (p_i - c) x f_i ~ [p_i - cbar]x f_i + [fbar_i]x (c - cbar),
+    exact when c = cbar, with error (cbar - c) x (f_i - fbar_i) otherwise.
+    Stage cost (Sec. II-B): CoM tracking on c, velocity tracking on
+    v = l_G / m (a weight Q_v / m^2 on l_G), angular-momentum regulation on
+    k_G (weights 1e-4 .. 1e-2); diagonal Q.  Inputs, contact sets, schedules and R are the 13-state
+    workload's."""
+    cd, nc = spec.contact_dim, spec.n_contacts
+    nu = nc * cd
+    k = np.arange(N + 1, dtype=np.float64)
+    psi0 = stack("psi0")
+    vcmd = 0.5 * np.stack([np.cos(psi0), np.sin(psi0), np.zeros_like(psi0)], -1)      # [nb,3]
+    cbar = np.zeros((nb, N + 1, 3))
+    cbar[..., 2] = COM_HEIGHT
+    cbar += k[None, :, None] * dt * vcmd[:, None, :]
+    # contact positions relative to the nominal CoM (world frame): the 13-state
+    # model's foot placement
+    off = stack("foot_off")                                                          # [nb,N,2,2]
+    lateral = np.array([0.1, -0.1])
+    Rz = _rot_z(psi)
+    lever = np.zeros((nb, N, nc, 3))
+    if cd == 6:
+        for f in range(2):
+            loc = np.zeros((nb, N, 3))
+            loc[..., 0] = off[..., f, 0]
+            loc[..., 1] = lateral[f] + off[..., f, 1]
+            loc[..., 2] = -COM_HEIGHT
+            lever[:, :, f] = np.einsum("bkij,bkj->bki", Rz, loc)
+    else:
+        corners = np.array([[1, 1], [1, -1], [-1, 1], [-1, -1]], dtype=np.float64)
+        corners = corners * np.array([FOOT_HALF_LENGTH, FOOT_HALF_WIDTH])
+        for f in range(2):
+            for c in range(4):
+                loc = np.zeros((nb, N, 3))
+                loc[..., 0] = off[..., f, 0] + corners[c, 0]
+                loc[..., 1] = lateral[f] + off[..., f, 1] + corners[c, 1]
+                loc[..., 2] = -COM_HEIGHT
+                lever[:, :, 4 * f + c] = np.einsum("bkij,bkj->bki", Rz, loc)
+    n_st = contact_stance.sum(-1)                                                    # [nb,N]
+    Fbar = np.zeros((nb, N, 3))
+    Fbar[..., 2] = np.where(n_st > 0, MASS * GRAVITY, 0.0)                          # sum of fbar_i
+
+    A = np.zeros((nb, N, NX9, NX9))
+    A[...] = np.eye(NX9)
+    A[..., 0:3, 3:6] = dt / MASS * np.eye(3)
+    A[..., 6:9, 0:3] = dt * _skew(Fbar)
+    Bm = np.zeros((nb, N, NX9, nu))
+    for i in range(nc):
+        c0 = i * cd
+        Bm[..., 3:6, c0:c0 + 3] = dt * np.eye(3)
+        Bm[..., 6:9, c0:c0 + 3] = dt * _skew(lever[:, :, i])
+        if cd == 6:
+            Bm[..., 6:9, c0 + 3:c0 + 6] = dt * np.eye(3)
+    e = np.zeros((nb, N, NX9))
+    e[..., 5] = -dt * MASS * GRAVITY
+    e[..., 6:9] = -dt * np.einsum("bkij,bkj->bki", _skew(Fbar), cbar[:, :N])
+    if spec.e_scale:
+        e += spec.e_scale * stack("e_noise")[..., 0:NX9]
+
+    q = stack("Q")[:, 0:NX9].copy()
+    q[:, 3:6] /= MASS ** 2
+    # angular momentum is regularised, not tracked hard: with weights of the
+    # order of the CoM weights the gravity torque about an offset CoM in
+    # single support drives the contact forces to their bounds
+    q[:, 6:9] *= 1e-4
+    Q = np.repeat(q[:, None, :], N, axis=1)
+    rn = stack("ry_noise")[..., 0:NX9]                                               # [nb,N,9]
+    ry = np.zeros((nb, N, NX9))
+    ry[..., 0:3] = cbar[:, 1:] + spec.ref_noise * rn[..., 0:3]
+    ry[..., 3:6] = MASS * (vcmd[:, None, :] + spec.ref_noise * rn[..., 3:6])
+    ry[..., 6:9] = spec.ref_noise * rn[..., 6:9]
+    x0n = stack("xi0_noise")[:, 0:NX9]
+    xi0 = np.zeros((nb, NX9))
+    xi0[:, 0:3] = cbar[:, 0] + spec.ref_noise * x0n[:, 0:3]
+    xi0[:, 3:6] = MASS * (vcmd + spec.ref_noise * x0n[:, 3:6])
+    xi0[:, 6:9] = spec.ref_noise * x0n[:, 6:9]
+    nominal = {"cbar": cbar, "lever": lever, "fbar_sum": Fbar}
+    return A, Bm, e, Q, ry, xi0, nominal
 
 
 def cone_coefficients(contact_dim: int, mu: float) -> tuple[list[int], list[float], int]:

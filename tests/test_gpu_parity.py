@@ -186,3 +186,13 @@ def test_large_batch_work_lists(pinmpc):
     assert np.all(out["status"] == 0) and out["kkt"].max() <= KKT_TOL
     assert dynamics_residual(batch, out) <= 1e-6
     compare(batch, out, [0, 4095, 4096, 9999, 16383])
+
+
+@pytest.mark.parametrize("spec", [W.centroidal9_walking(B=64, N=20, seed=41), W.centroidal9_small(B=64, N=10, seed=42)],
+                         ids=["cd9-points", "cd9-wrenches"])
+def test_nine_state_centroidal_model(pinmpc, spec):
+    # the paper's own 9-state model (Sec. II-A), linearised, both contact models
+    batch = W.generate(spec)
+    out = pinmpc.solve_workload(batch)
+    assert np.all(out["status"] == 0) and out["kkt"].max() <= KKT_TOL, out["status"]
+    compare(batch, out, [0, 13, 31, 63])

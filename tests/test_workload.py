@@ -47,3 +47,43 @@ def test_receding_step_shifts_stages():
         assert np.array_equal(new[:, -1], old[:, -1]), name
     assert np.array_equal(n.xi0, xi0) and np.array_equal(n.u_prev, up)
     assert np.array_equal(n.horizon, b.horizon)
+
+
+def _cd9_step(xi, f, tau, p, dt):
+    """One step of the discrete centroidal dynamics of Sec. II-A, as printed:
+    c+ = c + dt l/m,  l+ = l + dt (m g + sum f),  k+ = k + dt sum ((p - c) x f + tau)."""
+    c, l, k = xi[0:3], xi[3:6], xi[6:9]
+    g = np.array([0.0, 0.0, -W.GRAVITY])
+    cn = c + dt * l / W.MASS
+    ln = l + dt * (W.MASS * g + f.sum(0))
+    kn = k + dt * (np.cross(p - c, f).sum(0) + tau.sum(0))
+    return np.concatenate([cn, ln, kn])
+
+
+def test_cd9_linearisation_against_the_centroidal_dynamics():
+    # at c = cbar the linear model equals the nonlinear step for any l, k,
+    # forces; elsewhere it exceeds it by exactly dt (c - cbar) x sum(f - fbar)
+    rng = np.random.default_rng(11)
+    for spec in (W.centroidal9_walking(B=3, N=6), W.centroidal9_small(B=3, N=6)):
+        b = W.generate(spec)
+        cd, nc = spec.contact_dim, spec.n_contacts
+        A, Bm, e = b.A.astype(np.float64), b.Bm.astype(np.float64), b.e.astype(np.float64)
+        for i in range(3):
+            for k in range(6):
+                cbar = b.nominal["cbar"][i, k]
+                p = cbar + b.nominal["lever"][i, k]                      # [nc,3]
+                st = b.stance()[i, k]
+                fbar = np.zeros((nc, 3))
+                if st.any():
+                    fbar[st, 2] = W.MASS * W.GRAVITY / st.sum()
+                for dc_scale in (0.0, 0.05):
+                    xi = np.concatenate([cbar + dc_scale * rng.normal(size=3), rng.normal(size=6)])
+                    u = rng.normal(size=(nc, cd)) * 20.0
+                    u[~st] = 0.0
+                    f, tau = u[:, 0:3], (u[:, 3:6] if cd == 6 else np.zeros((nc, 3)))
+                    lin = A[i, k] @ xi + Bm[i, k] @ u.reshape(-1) + e[i, k]
+                    nonlin = _cd9_step(xi, f[st], tau[st], p[st], spec.dt)
+                    want = spec.dt * np.cross(xi[0:3] - cbar, (f - fbar)[st].sum(0)) if st.any() else 0.0
+                    got = lin.copy()
+                    got[6:9] -= want
+                    assert np.allclose(got, nonlin, rtol=0, atol=1e-4 * (1 + np.abs(nonlin).max())), (spec.contact_dim, i, k)
