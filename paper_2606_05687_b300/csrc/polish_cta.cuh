@@ -20,6 +20,7 @@
 namespace pinmpc {
 
 constexpr int kPT = 128;  // threads per polish CTA
+constexpr int kPivotBlock = 4;  // pivots eliminated per Gauss-Jordan step (divides nu)
 
 // Approximate reciprocal (PTX rcp.approx, relative error below 2^-22); used
 // for elimination pivots, whose rounding is far below the certificate's tolerance.
@@ -46,7 +47,7 @@ struct CtaSmem {
                          osv = al(oet + XP), odv = al(osv + XP), oSBT = al(odv + XP), oSAT = al(oSBT + NU * XP),
                          oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
                          oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oMC = al(ofree + 4),
-                         opcb = al(oMC + (NU + NK) * 32), oScanEnd = al(opcb + 2 * 32),
+                         opcb = al(oMC + (NU + NK) * 32), oScanEnd = al(opcb + 2 * kPivotBlock * 32),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + NU * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
                          ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
@@ -331,19 +332,26 @@ __device__ int cta_polish(const CCtx<D>& c) {
             }
         }
         __syncthreads();
-        // (4) Gauss-Jordan elimination without pivoting (M is SPD) over the
-        //     free columns only, by two warps (warps 0-1 or 2-3 by CTA parity,
-        //     so co-resident CTAs spread this phase over the SM's schedulers),
-        //     thread j holding all NU entries of column j in registers.  Step pp (fully
-        //     unrolled, so every register index is fixed; skipped uniformly
-        //     when column pp is eliminated): the owner of column pp publishes
-        //     it into a double-buffered vector, then every column takes
-        //     prj = X[pp][j] / X[pp][pp], X[a][j] -= X[a][pp] prj, X[pp][j] = prj
-        //     (column pp itself becomes the unit vector).  Afterwards column
-        //     NU + c holds column c of [K | kappa]; eliminated rows stay zero.
+        // (4) Gauss-Jordan elimination without pivoting (M is SPD), a block of
+        //     PB pivots (columns p0 .. p0 + PB - 1) per step, by two warps
+        //     (warps 0-1 or 2-3 by CTA parity, so co-resident CTAs spread this
+        //     phase over the SM's schedulers), thread j holding all NU entries
+        //     of column j in registers.  Step (fully unrolled, so every
+        //     register index is fixed; skipped uniformly when the whole block
+        //     is eliminated): the block's owners publish their columns into a
+        //     double-buffered set, then every column solves the PB x PB pivot
+        //     block for its block rows, M_bb y = x_b (Gaussian elimination,
+        //     no pivoting: the block is SPD), and takes x -= M_.b y, x_b = y
+        //     (the pivot columns become unit vectors).  An eliminated column
+        //     is already the unit vector and its row zero in every other
+        //     column, so the block solve reduces exactly to the free pivots.
+        //     Afterwards column NU + c holds column c of [K | kappa];
+        //     eliminated rows stay zero.
         const int gj = tid - ((blockIdx.x & 1) ? 64 : 0);  // column index in the eliminating warps
         if (gj >= 0 && gj < 64) {
+            constexpr int PB = kPivotBlock;
             static_assert(W <= 64, "elimination runs on two warps");
+            static_assert(NU % PB == 0, "pivot blocks tile the inputs");
             float* pcb = sm + CS::opcb;
             const bool act = gj < W;
             float xc[4 * (CP / 4)];
@@ -360,29 +368,57 @@ __device__ int cta_polish(const CCtx<D>& c) {
             }
             int bsel = 0;
 #pragma unroll
-            for (int pp = 0; pp < NU; ++pp) {
-                if ((fmask >> pp) & 1u) {
-                    float* buf = pcb + bsel * 32;
-                    if (gj == pp) {
+            for (int pq = 0; pq < NU / PB; ++pq) {
+                const int p0 = PB * pq;
+                if ((fmask >> p0) & ((1u << PB) - 1u)) {
+                    float* buf = pcb + bsel * (PB * 32);
+                    if (gj >= p0 && gj < p0 + PB) {
+                        float* dst = buf + (gj - p0) * 32;
 #pragma unroll
                         for (int q = 0; q < CP / 4; ++q)
-                            reinterpret_cast<float4*>(buf)[q] =
+                            reinterpret_cast<float4*>(dst)[q] =
                                 make_float4(xc[4 * q], xc[4 * q + 1], xc[4 * q + 2], xc[4 * q + 3]);
                     }
                     asm volatile("bar.sync 1, 64;" ::: "memory");
-                    float pc[4 * (CP / 4)];
+                    // m[i][j] = M[p0 + i][p0 + j] (column j of the block), y = x_b
+                    float m[PB][PB], y[PB];
+#pragma unroll
+                    for (int i = 0; i < PB; ++i) {
+                        y[i] = xc[p0 + i];
+#pragma unroll
+                        for (int j = 0; j < PB; ++j) m[i][j] = buf[j * 32 + p0 + i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < PB; ++i) {
+                        const float ip = rcp_approx(m[i][i]);
+#pragma unroll
+                        for (int r = i + 1; r < PB; ++r) {
+                            const float f = m[r][i] * ip;
+#pragma unroll
+                            for (int j = i + 1; j < PB; ++j) m[r][j] = fmaf(-f, m[i][j], m[r][j]);
+                            y[r] = fmaf(-f, y[i], y[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = PB - 1; i >= 0; --i) {
+                        float v = y[i];
+#pragma unroll
+                        for (int j = i + 1; j < PB; ++j) v = fmaf(-m[i][j], y[j], v);
+                        y[i] = v * rcp_approx(m[i][i]);
+                    }
 #pragma unroll
                     for (int q = 0; q < CP / 4; ++q) {
-                        const float4 t4 = reinterpret_cast<const float4*>(buf)[q];
-                        pc[4 * q + 0] = t4.x;
-                        pc[4 * q + 1] = t4.y;
-                        pc[4 * q + 2] = t4.z;
-                        pc[4 * q + 3] = t4.w;
-                    }
-                    const float prj = xc[pp] * rcp_approx(pc[pp]);
 #pragma unroll
-                    for (int a = 0; a < NU; ++a) xc[a] = fmaf(-pc[a], prj, xc[a]);
-                    xc[pp] = prj;
+                        for (int j = 0; j < PB; ++j) {
+                            const float4 cj = reinterpret_cast<const float4*>(buf + j * 32)[q];
+                            if (4 * q + 0 < NU) xc[4 * q + 0] = fmaf(-cj.x, y[j], xc[4 * q + 0]);
+                            if (4 * q + 1 < NU) xc[4 * q + 1] = fmaf(-cj.y, y[j], xc[4 * q + 1]);
+                            if (4 * q + 2 < NU) xc[4 * q + 2] = fmaf(-cj.z, y[j], xc[4 * q + 2]);
+                            if (4 * q + 3 < NU) xc[4 * q + 3] = fmaf(-cj.w, y[j], xc[4 * q + 3]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < PB; ++i) xc[p0 + i] = y[i];
                     bsel ^= 1;
                 }
             }
