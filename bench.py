@@ -470,6 +470,45 @@ def run_gpu(args):
                             f"{reps} calls each), the landmark epilogue of Sec. II-C"}
         lmo.close()
 
+    graph = None
+    if not args.device_only:
+        # CUDA-graph replay (mpc_set_graph_mode) against direct launches: the
+        # host time to enqueue one solve of B, and the latency of a small batch
+        # (64 environments: set_stages, solve, get_traj, synchronise), medians
+        s0 = streams[0]
+        sub = batch.subset(range(64))
+        t_sub = pinmpc.device_inputs(sub, "cuda")
+        res = {}
+        for mode in ("direct", "graph"):
+            big = solvers[0]
+            big.set_graph_mode(mode == "graph")
+            host_us = []
+            for k in range(12):
+                s0.synchronize()
+                h0 = time.perf_counter()
+                big.solve(B, stream=s0)
+                host_us.append((time.perf_counter() - h0) * 1e6)
+            s0.synchronize()
+            small = pinmpc.solver_for(sub, max_iter=args.max_iter)
+            small.set_graph_mode(mode == "graph")
+            xo = torch.empty((64, N, 13), device=dev)
+            uo = torch.empty((64, N, 24), device=dev)
+            lat = []
+            for k in range(40):
+                s0.synchronize()
+                h0 = time.perf_counter()
+                small.set_stages(64, N, **t_sub, stream=s0)
+                small.solve(64, stream=s0)
+                small.get_traj(xo, uo, None, None, None, None, stream=s0)
+                s0.synchronize()
+                lat.append((time.perf_counter() - h0) * 1e3)
+            small.close()
+            res[mode] = {"host_us_per_solve": float(np.median(host_us[2:])),
+                         "small_batch_ms": float(np.median(lat[5:]))}
+        solvers[0].set_graph_mode(False)
+        graph = dict(res, what="host time to enqueue one solve of B (median), and the wall-clock latency of a 64-environment "
+                               "set_stages/solve/get_traj round trip (median), direct launches vs one CUDA-graph launch")
+
     if rank != 0:
         return
     # roofline of the dominant kernel from the live per-kernel times (each
@@ -499,6 +538,7 @@ def run_gpu(args):
         "single_stream": single,
         "served": served,
         "landmarks": landmark,
+        "graph": graph,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),

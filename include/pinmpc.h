@@ -207,6 +207,19 @@ mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream);
 mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable);
 mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, int32_t reset);
 
+/* CUDA-graph replay of the solve (no counterpart in the paper; a launch-cost
+ * aid).  With enable != 0, mpc_solve_batch records its device work (flag
+ * resets, the factor kernel and the whole round schedule) into a CUDA graph
+ * on an internal stream the first time it meets a (B, N, warm-start count)
+ * combination, keeps up to 4 such graphs, and thereafter enqueues the
+ * solve as one graph launch on `stream`: the results are bit-identical to
+ * the direct launches, the host cost per solve drops to one call.  While
+ * per-kernel timing is on, solves use direct launches.  enable = 0 frees
+ * the graphs.  mpc_get_graph_stats: graphs captured and solves replayed so
+ * far (either pointer may be NULL). */
+mpc_status mpc_set_graph_mode(mpc_handle* h, int32_t enable);
+mpc_status mpc_get_graph_stats(mpc_handle* h, int64_t* captures, int64_t* replays);
+
 /* Solve a batch without allocating any device memory (no counterpart in the
  * paper; this is a deployment aid).  For callers that may not allocate: code
  * inside someone else's captured CUDA graph, a simulator step that owns a

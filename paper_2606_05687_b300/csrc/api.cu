@@ -176,6 +176,17 @@ struct mpc_handle {
         cudaEvent_t start, stop;
     };
     bool timing = false;
+    // CUDA-graph replay of the solve (mpc_set_graph_mode): the enqueued
+    // sequence captured on capture_stream, one executable graph per
+    // (B, N, double buffering, warm-start count), most recent last
+    struct SolveGraph {
+        int B, N, dbl, warm_B;
+        cudaGraphExec_t exec;
+    };
+    bool graph_mode = false;
+    cudaStream_t capture_stream = nullptr;
+    std::vector<SolveGraph> graphs;
+    int64_t graph_captures = 0, graph_replays = 0;
     std::vector<cudaEvent_t> event_pool;
     std::vector<TimedLaunch> pending;
     double kernel_ms[MPC_KERNEL_CLASSES] = {};
@@ -522,34 +533,11 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     return MPC_OK;
 }
 
-mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
-    if (!h) return MPC_ERR_INVALID_ARG;
-    if (!h->have_stages) return fail(h, MPC_ERR_STATE, "mpc_solve_batch before mpc_set_stages");
-    if (B < 1 || B > h->B_set) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_set);
+// The solve's device work for instances [0, B) on stream st: flag resets,
+// the factor kernel and the whole round schedule (no host synchronisation).
+static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStream_t st, int round_smem) {
     const mpc_config& c = h->cfg;
-    cudaError_t e = cudaSetDevice(c.device);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    RoundArgs r{};
-    r.rec = h->rec; r.irec = h->irec; r.n_rec = c.N_max; r.N = h->N_set;
-    r.rho = c.rho; r.sigma = c.u_scale; r.kkt_tol = c.kkt_tol; r.eta = c.restart_eta;
-    r.dx = c.foot_half_length; r.dy = c.foot_half_width;
-    r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
-    r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
-    r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
-    r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
-    r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
-    r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
-    // double-buffered records and factors (TMA prefetch) when they fit
-    const int smem_single = h->shape.round_smem(h->N_set, false), smem_dbl = h->shape.round_smem(h->N_set, true);
-    const bool dbl = smem_dbl <= h->optin_smem;
-    const int round_smem = dbl ? smem_dbl : smem_single;
-    if (round_smem > h->round_attr) {
-        if ((e = h->shape.set_round_attrs(round_smem, h->shape.polish_smem(c.N_max))) != cudaSuccess)
-            return cuda_fail(h, e, "cudaFuncSetAttribute");
-        h->round_attr = round_smem;
-    }
-    r.dbl = dbl ? 1 : 0;
+    cudaError_t e;
     const int polish_smem = h->shape.polish_smem(h->N_set);
     if ((e = cudaMemsetAsync(h->done, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");
@@ -600,6 +588,77 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
             return cuda_fail(h, e, "polish kernel launch");
         if (m1 >= c.max_iter) break;
         m0 = m1;
+    }
+    return MPC_OK;
+}
+
+mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_stages) return fail(h, MPC_ERR_STATE, "mpc_solve_batch before mpc_set_stages");
+    if (B < 1 || B > h->B_set) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_set);
+    const mpc_config& c = h->cfg;
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    RoundArgs r{};
+    r.rec = h->rec; r.irec = h->irec; r.n_rec = c.N_max; r.N = h->N_set;
+    r.rho = c.rho; r.sigma = c.u_scale; r.kkt_tol = c.kkt_tol; r.eta = c.restart_eta;
+    r.dx = c.foot_half_length; r.dy = c.foot_half_width;
+    r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
+    r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
+    r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
+    r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
+    r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
+    r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
+    // double-buffered records and factors (TMA prefetch) when they fit
+    const int smem_single = h->shape.round_smem(h->N_set, false), smem_dbl = h->shape.round_smem(h->N_set, true);
+    const bool dbl = smem_dbl <= h->optin_smem;
+    const int round_smem = dbl ? smem_dbl : smem_single;
+    if (round_smem > h->round_attr) {
+        if ((e = h->shape.set_round_attrs(round_smem, h->shape.polish_smem(c.N_max))) != cudaSuccess)
+            return cuda_fail(h, e, "cudaFuncSetAttribute");
+        h->round_attr = round_smem;
+    }
+    r.dbl = dbl ? 1 : 0;
+    r.warm_B = (h->warm_N == h->N_set) ? std::min(h->warm_B, B) : 0;
+    mpc_status ms = MPC_OK;
+    if (h->graph_mode && !h->timing) {
+        // replay the captured sequence for this key, capturing it first if new
+        const int key_dbl = r.dbl;
+        auto it = std::find_if(h->graphs.begin(), h->graphs.end(), [&](const mpc_handle::SolveGraph& g) {
+            return g.B == B && g.N == h->N_set && g.dbl == key_dbl && g.warm_B == r.warm_B;
+        });
+        if (it == h->graphs.end()) {
+            if (!h->capture_stream &&
+                (e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaStreamCreateWithFlags");
+            if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(h, e, "cudaStreamBeginCapture");
+            ms = enqueue_solve(h, B, r, h->capture_stream, round_smem);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(h->capture_stream, &g);
+            if (ms != MPC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return ms;
+            }
+            if (ee != cudaSuccess) return cuda_fail(h, ee, "cudaStreamEndCapture");
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+            if (h->graphs.size() >= 4) {
+                cudaGraphExecDestroy(h->graphs.front().exec);
+                h->graphs.erase(h->graphs.begin());
+            }
+            h->graphs.push_back({B, h->N_set, key_dbl, r.warm_B, ex});
+            ++h->graph_captures;
+            it = h->graphs.end() - 1;
+        }
+        if ((e = cudaGraphLaunch(it->exec, st)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+        ++h->graph_replays;
+    } else {
+        ms = enqueue_solve(h, B, r, st, round_smem);
+        if (ms != MPC_OK) return ms;
     }
     h->have_solution = true;
     h->B_solved = B;
@@ -676,6 +735,28 @@ mpc_status mpc_warm_start(mpc_handle* h, int32_t shift, void* stream) {
     return MPC_OK;
 }
 
+static void drop_graphs(mpc_handle* h) {
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+mpc_status mpc_set_graph_mode(mpc_handle* h, int32_t enable) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    h->graph_mode = enable != 0;
+    if (!h->graph_mode) {
+        cudaSetDevice(h->cfg.device);
+        drop_graphs(h);
+    }
+    return MPC_OK;
+}
+
+mpc_status mpc_get_graph_stats(mpc_handle* h, int64_t* captures, int64_t* replays) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (captures) *captures = h->graph_captures;
+    if (replays) *replays = h->graph_replays;
+    return MPC_OK;
+}
+
 mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable) {
     if (!h) return MPC_ERR_INVALID_ARG;
     h->timing = enable != 0;
@@ -708,6 +789,8 @@ void mpc_destroy(mpc_handle* h) {
     }
     for (cudaEvent_t ev : h->event_pool) cudaEventDestroy(ev);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    drop_graphs(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->staged) cudaEventDestroy(h->staged);
     if (h->consumed) cudaEventDestroy(h->consumed);
     cudaFree(h->out_piv);

@@ -73,6 +73,10 @@ def load() -> ctypes.CDLL:
     lib.mpc_get_stats.restype = ctypes.c_int
     lib.mpc_warm_start.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
     lib.mpc_warm_start.restype = ctypes.c_int
+    lib.mpc_set_graph_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.mpc_set_graph_mode.restype = ctypes.c_int
+    lib.mpc_get_graph_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.mpc_get_graph_stats.restype = ctypes.c_int
     lib.mpc_get_pivots.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.mpc_get_pivots.restype = ctypes.c_int
     lib.mpc_set_kernel_timing.argtypes = [ctypes.c_void_p, ctypes.c_int32]
@@ -182,6 +186,15 @@ class Solver:
     def get_pivots(self, pivots=None, stream=None):
         self._check(self.lib.mpc_get_pivots(self.h, _ptr(pivots), _stream_ptr(stream)),
                     "mpc_get_pivots")
+
+    def set_graph_mode(self, enable: bool):
+        self._check(self.lib.mpc_set_graph_mode(self.h, 1 if enable else 0), "mpc_set_graph_mode")
+
+    def graph_stats(self):
+        """(graphs captured, solves replayed) so far."""
+        c, r = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.mpc_get_graph_stats(self.h, ctypes.byref(c), ctypes.byref(r)), "mpc_get_graph_stats")
+        return c.value, r.value
 
     def set_kernel_timing(self, enable: bool):
         self._check(self.lib.mpc_set_kernel_timing(self.h, 1 if enable else 0), "mpc_set_kernel_timing")
