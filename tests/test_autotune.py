@@ -1,0 +1,35 @@
+"""Schedule autotuner host logic (no device): candidate order and selection."""
+from paper_2606_05687_b300 import autotune as A
+
+
+def test_candidates_start_at_the_defaults_and_cover_the_grid():
+    c = A.candidates()
+    n = 1
+    for v in A.DEFAULT_GRID.values():
+        n *= len(v)
+    assert len(c) == n and len({tuple(sorted(x.items())) for x in c}) == n
+    assert c[0] == A.LIBRARY_DEFAULTS
+    # one-parameter neighbours come before two-parameter ones
+    diffs = [sum(1 for k in A.LIBRARY_DEFAULTS if x[k] != A.LIBRARY_DEFAULTS[k]) for x in c]
+    assert diffs == sorted(diffs)
+    assert len(A.candidates(limit=5)) == 5
+
+
+def test_select_best_takes_the_fastest_fully_certified_entry():
+    t = [{"config": {"a": 1}, "ms": 3.0, "certified": 10, "instances": 10},
+         {"config": {"a": 2}, "ms": 1.0, "certified": 9, "instances": 10},
+         {"config": {"a": 3}, "ms": 2.0, "certified": 10, "instances": 10},
+         {"config": {"a": 4}, "ms": 2.0, "certified": 10, "instances": 10}]
+    assert A.select_best(t)["config"] == {"a": 3}
+    # with no fully certified entry, the most certified one wins
+    assert A.select_best([t[1], dict(t[0], certified=8)])["config"] == {"a": 2}
+    assert A.select_best([]) is None
+
+
+def test_library_defaults_match_the_c_defaults():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05687_b300 import pinmpc
+    cfg = pinmpc.default_config(13, 8, 3, 16, 20)
+    for k, v in A.LIBRARY_DEFAULTS.items():
+        assert abs(getattr(cfg, k) - v) < 1e-9, k
