@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPC QP solves/s at B=4096 N=20 (KKT≤1e-5); served p50/p99 solve latency"
 B_BENCH, N_BENCH, SEED = 4096, 20, 1002
-INFLIGHT = 2  # batches in flight on separate handles and streams
+INFLIGHT = 3  # batches in flight on separate handles and streams (--inflight)
 KKT_TOL = 1e-5
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -577,12 +577,14 @@ def run_gpu(args):
 
 
 def main():
+    global INFLIGHT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--inflight", type=int, default=INFLIGHT, help="batches in flight (handles and streams)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -590,6 +592,7 @@ def main():
                     help="profiling aid: only the device-resident steps (no CPU baseline, no e2e leg); "
                          "the line it prints is not a bench result")
     args = ap.parse_args()
+    INFLIGHT = max(1, args.inflight)
     if args.impl == "reference":
         run_reference(args)
     else:
