@@ -207,6 +207,31 @@ mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream);
 mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable);
 mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, int32_t reset);
 
+/* Per-environment warm state (no counterpart in the paper; it extends the
+ * receding-horizon warm start of mpc_warm_start to callers that re-form
+ * their batches, such as a server that batches whichever environments have
+ * pending requests, so an environment lands in a different slot each time).
+ * The state of one instance is its final ADMM iterate (both buffers of
+ * (z, v, theta, beta, lambda)) and acceleration scalars:
+ * mpc_state_floats(h, N) floats at horizon stride N (0 for a null handle or
+ * N outside [1, N_max]).
+ *   mpc_save_state: after a solve, row idx[b] of `store` receives instance
+ *     b's state for b < B (B <= the solved batch), its stages moved `shift`
+ *     stages towards the start of its horizon as in mpc_warm_start; idx NULL
+ *     means row b.  An instance whose solve failed saves a cold (zero) state.
+ *   mpc_load_state: instances b < B of the batch set by mpc_set_stages
+ *     start the next mpc_solve_batch from row idx[b] of `store` (saved at
+ *     the same N); the others start cold.  Put the environments with saved
+ *     state first in the batch.
+ * `store` is device memory of `rows` rows owned by the caller; indices
+ * outside [0, rows) are not written (save) or start cold (load); both calls
+ * are asynchronous on `stream`. */
+int64_t mpc_state_floats(mpc_handle* h, int32_t N);
+mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32_t rows, int32_t B, int32_t shift,
+                          void* stream);
+mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx, int32_t rows, int32_t B,
+                          void* stream);
+
 /* CUDA-graph replay of the solve (no counterpart in the paper; a launch-cost
  * aid).  With enable != 0, mpc_solve_batch records its device work (flag
  * resets, the factor kernel and the whole round schedule) into a CUDA graph

@@ -13,6 +13,7 @@
 #include "admm.cuh"
 #include "polish_cta.cuh"
 #include "internal.h"
+#include "warm_state.cuh"
 
 using namespace pinmpc;
 
@@ -42,6 +43,9 @@ struct Shape {
     void (*launch_warm_shift)(float* state, const float* rec, int irec, int n_rec, int B, int N, int shift,
                               cudaStream_t s);
     cudaError_t (*set_warm_attr)(int bytes);
+    void (*launch_state_copy)(const float* src, const int* sidx, int src_rows, float* dst, const int* didx, int dst_rows,
+                              const float* rec, int irec, int n_rec, int B, int N, int shift, cudaStream_t s);
+    cudaError_t (*set_state_copy_attr)(int bytes);
 };
 
 template <class D>
@@ -102,11 +106,21 @@ cudaError_t set_warm_attr_t(int bytes) {
     return cudaFuncSetAttribute(warm_shift_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 template <class D>
+void launch_state_copy_t(const float* src, const int* sidx, int src_rows, float* dst, const int* didx, int dst_rows,
+                         const float* rec, int irec, int n_rec, int B, int N, int shift, cudaStream_t s) {
+    state_copy_kernel<D><<<B, 256, RoundState<D>::var_floats(N) * sizeof(float), s>>>(
+        src, sidx, src_rows, dst, didx, dst_rows, rec, irec, n_rec, N, shift);
+}
+template <class D>
+cudaError_t set_state_copy_attr_t(int bytes) {
+    return cudaFuncSetAttribute(state_copy_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <class D>
 Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           launch_pack_t<D>,     polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
                  cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>, launch_warm_shift_t<D>,
-                 set_warm_attr_t<D>};
+                 set_warm_attr_t<D>, launch_state_copy_t<D>, set_state_copy_attr_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -731,6 +745,48 @@ mpc_status mpc_warm_start(mpc_handle* h, int32_t shift, void* stream) {
     h->shape.launch_warm_shift(h->state, h->rec, h->irec, h->cfg.N_max, h->B_solved, h->N_set, shift, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "warm-start kernel launch");
     h->warm_B = h->B_solved;
+    h->warm_N = h->N_set;
+    return MPC_OK;
+}
+
+int64_t mpc_state_floats(mpc_handle* h, int32_t N) {
+    if (!h || N < 1 || N > h->cfg.N_max) return 0;
+    return h->shape.state_floats(N);
+}
+
+mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32_t rows, int32_t B, int32_t shift,
+                          void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_solution) return fail(h, MPC_ERR_STATE, "mpc_save_state before mpc_solve_batch");
+    if (!store || rows < 1) return fail(h, MPC_ERR_INVALID_ARG, "null store or rows < 1");
+    if (B < 1 || B > h->B_solved) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_solved);
+    if (shift < 0 || shift >= h->N_set) return fail(h, MPC_ERR_INVALID_ARG, "shift=%d outside [0, N=%d)", shift, h->N_set);
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const int smem = h->shape.state_floats(h->N_set) * (int)sizeof(float);
+    if (smem > 48 * 1024 && (e = h->shape.set_state_copy_attr(smem)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaFuncSetAttribute");
+    h->shape.launch_state_copy(h->state, nullptr, h->B_solved, store, idx, rows, h->rec, h->irec, h->cfg.N_max, B,
+                               h->N_set, shift, static_cast<cudaStream_t>(stream));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state copy launch");
+    return MPC_OK;
+}
+
+mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx, int32_t rows, int32_t B,
+                          void* stream) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (!h->have_stages) return fail(h, MPC_ERR_STATE, "mpc_load_state before mpc_set_stages");
+    if (!store || rows < 1) return fail(h, MPC_ERR_INVALID_ARG, "null store or rows < 1");
+    if (B < 1 || B > h->B_set) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_set);
+    cudaError_t e = cudaSetDevice(h->cfg.device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const int smem = h->shape.state_floats(h->N_set) * (int)sizeof(float);
+    if (smem > 48 * 1024 && (e = h->shape.set_state_copy_attr(smem)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaFuncSetAttribute");
+    h->shape.launch_state_copy(store, idx, rows, h->state, nullptr, h->B_set, nullptr, 0, 0, B, h->N_set, 0,
+                               static_cast<cudaStream_t>(stream));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "state copy launch");
+    h->warm_B = B;
     h->warm_N = h->N_set;
     return MPC_OK;
 }

@@ -73,6 +73,14 @@ def load() -> ctypes.CDLL:
     lib.mpc_get_stats.restype = ctypes.c_int
     lib.mpc_warm_start.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
     lib.mpc_warm_start.restype = ctypes.c_int
+    lib.mpc_state_floats.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+    lib.mpc_state_floats.restype = ctypes.c_int64
+    lib.mpc_save_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_int32, ctypes.c_void_p]
+    lib.mpc_save_state.restype = ctypes.c_int
+    lib.mpc_load_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_void_p]
+    lib.mpc_load_state.restype = ctypes.c_int
     lib.mpc_set_graph_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_graph_mode.restype = ctypes.c_int
     lib.mpc_get_graph_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -186,6 +194,19 @@ class Solver:
     def get_pivots(self, pivots=None, stream=None):
         self._check(self.lib.mpc_get_pivots(self.h, _ptr(pivots), _stream_ptr(stream)),
                     "mpc_get_pivots")
+
+    def state_floats(self, N: int) -> int:
+        return int(self.lib.mpc_state_floats(self.h, N))
+
+    def save_state(self, store, idx, B: int, shift: int = 1, stream=None):
+        """Rows idx[b] of the device tensor `store` receive instance b's state (b < B)."""
+        self._check(self.lib.mpc_save_state(self.h, _ptr(store), _ptr(idx), store.shape[0], B, shift,
+                                            _stream_ptr(stream)), "mpc_save_state")
+
+    def load_state(self, store, idx, B: int, stream=None):
+        """Instances b < B of the next solve start from rows idx[b] of `store`."""
+        self._check(self.lib.mpc_load_state(self.h, _ptr(store), _ptr(idx), store.shape[0], B, _stream_ptr(stream)),
+                    "mpc_load_state")
 
     def set_graph_mode(self, enable: bool):
         self._check(self.lib.mpc_set_graph_mode(self.h, 1 if enable else 0), "mpc_set_graph_mode")

@@ -13,9 +13,14 @@ queue), so the host loop costs per batch, not per request.
 
 Every instance of a batch is solved independently, so a request's result
 does not depend on which other requests share its batch (the tests check
-this bit for bit).  A batch starts every instance cold: the receding-horizon
-warm start (mpc_warm_start) keeps state per batch slot, and a continuously
-re-formed batch has no stable slots.
+this bit for bit).  Without `warm_shift` every request starts cold.  With
+it, the server keeps each environment's solver state in a device store
+(mpc_save_state / mpc_load_state): a request of an environment solved
+before starts from its last state moved `warm_shift` stages (1 when each
+request is the environment's next MPC step), environments with a state
+are placed first in their batch, and `reset(envs)` makes the next request
+of those environments cold (a new episode).  Two requests of one
+environment in the same batch both start from its state before the batch.
 """
 from __future__ import annotations
 
@@ -40,7 +45,8 @@ class BatchServer:
     """
 
     def __init__(self, pool: Dict[str, "object"], nx: int, nc: int, contact_dim: int, B_max: int, N: int,
-                 n_handles: int = 2, clock: Callable[[], float] = time.perf_counter, **overrides):
+                 n_handles: int = 2, clock: Callable[[], float] = time.perf_counter,
+                 warm_shift: Optional[int] = None, **overrides):
         import torch
         self.torch = torch
         self.pool = pool
@@ -59,7 +65,14 @@ class BatchServer:
                         kkt=torch.empty(B_max, dtype=torch.float32, device=self.device))
             status_host = torch.empty(B_max, dtype=torch.int32).pin_memory()
             self.handles.append(dict(solver=solver, stream=torch.cuda.Stream(self.device), inputs=inputs,
-                                     outs=outs, status_host=status_host, busy=None, event=None))
+                                     outs=outs, status_host=status_host, busy=None, event=None, perm=None))
+        self.warm_shift = warm_shift
+        self.warm_loads = 0
+        if warm_shift is not None:
+            n_env = pool["A"].shape[0]
+            rows = self.handles[0]["solver"].state_floats(N)
+            self.store = torch.zeros((n_env, rows), dtype=torch.float32, device=self.device)
+            self.has_state = np.zeros(n_env, dtype=bool)
         cap = 1 << 16
         self.env = np.zeros(cap, np.int64)
         self.t_arrival = np.zeros(cap)
@@ -98,38 +111,62 @@ class BatchServer:
     def busy(self) -> bool:
         return any(h["busy"] is not None for h in self.handles)
 
+    def reset(self, envs):
+        """The next request of each of `envs` starts cold (a new episode)."""
+        if self.warm_shift is not None:
+            self.has_state[np.atleast_1d(np.asarray(envs, np.int64))] = False
+
     def _dispatch(self, h):
         torch = self.torch
         lo = self.head
         hi = min(self.n, lo + self.B_max)
         self.head = hi
         B = hi - lo
+        envs = self.env[lo:hi]
+        perm = None
+        n_warm = 0
+        if self.warm_shift is not None:
+            # environments with a saved state first (slots [0, n_warm))
+            warm = self.has_state[envs]
+            perm = np.argsort(~warm, kind="stable")
+            envs = envs[perm]
+            n_warm = int(warm.sum())
         with torch.cuda.stream(h["stream"]):
-            idx = torch.from_numpy(self.env[lo:hi]).to(self.device, non_blocking=True)
+            idx = torch.from_numpy(envs.astype(np.int32)).to(self.device, non_blocking=True)
+            idx64 = idx.long()
             for k in STAGE_KEYS:
-                torch.index_select(self.pool[k], 0, idx, out=h["inputs"][k][:B])
+                torch.index_select(self.pool[k], 0, idx64, out=h["inputs"][k][:B])
         view = {k: h["inputs"][k][:B] for k in STAGE_KEYS}
         s = h["solver"]
         s.set_stages(B, self.N, **view, stream=h["stream"])
+        if n_warm:
+            s.load_state(self.store, idx, n_warm, stream=h["stream"])
+            self.warm_loads += n_warm
         s.solve(B, stream=h["stream"])
+        if self.warm_shift is not None:
+            s.save_state(self.store, idx, B, shift=self.warm_shift, stream=h["stream"])
+            self.has_state[envs] = True
+            h["idx_keep"] = idx
         o = h["outs"]
         s.get_traj(xi=o["xi"], u=o["u"], status=o["status"], kkt=o["kkt"], stream=h["stream"])
         with torch.cuda.stream(h["stream"]):
             h["status_host"][:B].copy_(o["status"][:B], non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(h["stream"])
-        h["busy"], h["event"] = (lo, hi), ev
+        h["busy"], h["event"], h["perm"] = (lo, hi), ev, perm
         self.batches += 1
 
     def _retire(self, h, now):
         lo, hi = h["busy"]
+        # slot i holds request lo + order[i]
+        order = h["perm"] if h["perm"] is not None else np.arange(hi - lo)
         self.t_done[lo:hi] = now
-        self.status[lo:hi] = h["status_host"][:hi - lo].numpy()
+        self.status[lo + order] = h["status_host"][:hi - lo].numpy()
         if self.keep_results:
             o = {k: h["outs"][k][:hi - lo].cpu().numpy() for k in ("u", "xi", "kkt")}
             for i in range(hi - lo):
-                self.results[lo + i] = {k: o[k][i] for k in o}
-        h["busy"], h["event"] = None, None
+                self.results[lo + int(order[i])] = {k: o[k][i] for k in o}
+        h["busy"], h["event"], h["perm"] = None, None, None
 
     def step(self):
         """One pass of the serving loop: retire finished batches, start new ones."""

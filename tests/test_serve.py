@@ -59,3 +59,68 @@ def test_short_load_run(pinmpc):
     assert rep["certified"] == rep["requests"] > 0
     assert rep["p99_ms"] >= rep["p50_ms"] > 0
     srv.close()
+
+
+@pytest.mark.gpu
+def test_saved_state_equals_handle_warm_start_across_slots(pinmpc):
+    # mpc_save_state / mpc_load_state move each environment's state between
+    # slots exactly: a permuted re-batch starts from the same iterate as the
+    # in-place receding warm start
+    import torch
+    batch = W.generate(W.rl_scale_walking(B=48, N=20, seed=23))
+    a = pinmpc.solver_for(batch)
+    first = pinmpc.solve_workload(batch, solver=a)
+    nxt = batch.receding(first["xi"][:, 0], first["u"][:, 0])
+    a.warm_start(1)
+    ref = pinmpc.solve_workload(nxt, solver=a)
+    b = pinmpc.solver_for(batch)
+    pinmpc.solve_workload(batch, solver=b)
+    rng = np.random.default_rng(4)
+    rows = rng.permutation(64)[:48].astype(np.int32)                 # env e -> store row rows[e]
+    store = torch.zeros((64, b.state_floats(20)), device="cuda")
+    b.save_state(store, torch.from_numpy(rows).cuda(), 48, shift=1)
+    q = rng.permutation(48)                                           # slot s of the next batch holds env q[s]
+    b.set_stages(48, 20, **pinmpc.device_inputs(nxt.subset(q)))
+    b.load_state(store, torch.from_numpy(rows[q]).cuda(), 48)
+    b.solve(48)
+    u = torch.empty((48, 20, 24), device="cuda")
+    it = torch.empty(48, dtype=torch.int32, device="cuda")
+    b.get_traj(None, u, None, it, None, None)
+    torch.cuda.synchronize()
+    assert np.array_equal(u.cpu().numpy(), ref["u"][q]) and np.array_equal(it.cpu().numpy(), ref["iters"][q])
+    a.close()
+    b.close()
+
+
+@pytest.mark.gpu
+def test_served_warm_state_and_resets(pinmpc):
+    # with warm_shift 0 on unchanged stage data, an environment's second request
+    # starts from its first solution (as a handle's warm_start(0) would) and a
+    # reset one starts cold again, bit for bit, whatever the batching
+    from paper_2606_05687_b300.serve import BatchServer
+    batch = W.generate(W.rl_scale_walking(B=40, N=20, seed=24))
+    s = pinmpc.solver_for(batch)
+    cold = pinmpc.solve_workload(batch, solver=s)
+    s.warm_start(0)
+    warm = pinmpc.solve_workload(batch, solver=s)
+    s.close()
+    srv = BatchServer(pinmpc.device_inputs(batch), batch.nx, batch.nc, batch.contact_dim, B_max=16, N=batch.N,
+                      n_handles=2, warm_shift=0)
+    srv.keep_results = True
+    first = list(range(40))
+    srv.submit(first)
+    srv.drain()
+    srv.reset([3, 7])
+    second = [7, 39, 0, 3, 12] + list(range(13, 39, 2))
+    for e in second[:3]:
+        srv.submit(e)
+    srv.submit(second[3:])
+    srv.drain()
+    assert srv.warm_loads == len(second) - 2
+    for r, e in enumerate(first):
+        assert srv.status[r] == 0 and np.array_equal(srv.results[r]["u"], cold["u"][e])
+    for i, e in enumerate(second):
+        r = len(first) + i
+        want = cold if e in (3, 7) else warm
+        assert srv.status[r] == 0 and np.array_equal(srv.results[r]["u"], want["u"][e]), e
+    srv.close()
