@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MPC QP solves/s at B=4096 N=20 (KKT≤1e-5); served p50/p99 solve latency"
 B_BENCH, N_BENCH, SEED = 4096, 20, 1002
 INFLIGHT = 3  # batches in flight on separate handles and streams (--inflight)
+SERVE_HANDLES = 4  # handles of the served-latency leg (requests answered as their round ends)
 KKT_TOL = 1e-5
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -431,9 +432,10 @@ def run_gpu(args):
     if not args.device_only and world == 1:
         # served latency: single-environment requests arriving as a Poisson
         # stream at 70 % of the measured capacity for 1 s, continuously batched
-        # (up to B per batch) over two handles
+        # (up to B per batch) over SERVE_HANDLES handles, each request answered
+        # when the round that certifies its instance ends
         from paper_2606_05687_b300.serve import BatchServer, poisson_arrivals, serve_load
-        srv = BatchServer(t, batch.nx, batch.nc, batch.contact_dim, B_max=B, N=N, n_handles=INFLIGHT,
+        srv = BatchServer(t, batch.nx, batch.nc, batch.contact_dim, B_max=B, N=N, n_handles=SERVE_HANDLES,
                           max_iter=args.max_iter)
         serve_load(srv, poisson_arrivals(0.7 * value, 0.2, B, seed=SEED + 1))  # warm-up
         served = serve_load(srv, poisson_arrivals(0.7 * value, 1.0, B, seed=SEED))

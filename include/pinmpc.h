@@ -62,7 +62,9 @@ enum {
     MPC_NONFINITE = 2,  /* NaN/Inf in this instance's inputs */
     MPC_BAD_SET = 3,    /* empty contact set (n_max < 0 or mu < 0 on a stance contact) */
     MPC_TIMEOUT = 4,    /* reserved for bounded device-side waits */
-    MPC_BAD_HORIZON = 5 /* horizon[b] outside [1, N] */
+    MPC_BAD_HORIZON = 5, /* horizon[b] outside [1, N] */
+    MPC_RUNNING = -1     /* not finished yet: read before the solve has passed
+                            the round that finishes the instance */
 };
 
 /* Solver configuration; fill with mpc_default_config then adjust. */
@@ -206,6 +208,18 @@ mpc_status mpc_get_pivots(mpc_handle* h, int32_t* pivots, void* stream);
 #define MPC_KERNEL_CLASSES 4
 mpc_status mpc_set_kernel_timing(mpc_handle* h, int32_t enable);
 mpc_status mpc_get_kernel_times(mpc_handle* h, double* ms, int64_t* launches, int32_t reset);
+
+/* Early results (no counterpart in the paper; for servers that answer each
+ * request as soon as its instance is certified).  Every instance's status
+ * reads MPC_RUNNING from the start of mpc_solve_batch until the round that
+ * finishes it writes its final status, trajectory and certificate.  With
+ * events[r] (cudaEvent_t, caller-owned; NULL entries skipped) for r < n,
+ * every later mpc_solve_batch records events[r] on its stream right after
+ * round r (checks at check_start, then the growing intervals): work waiting
+ * on it (mpc_get_traj on another stream, for instance) sees the instances
+ * finished by then with their final results.  n = 0 clears the events;
+ * changing them frees the cached solve graphs. */
+mpc_status mpc_set_round_events(mpc_handle* h, void* const* events, int32_t n);
 
 /* Per-environment warm state (no counterpart in the paper; it extends the
  * receding-horizon warm start of mpc_warm_start to callers that re-form

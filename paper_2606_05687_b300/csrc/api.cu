@@ -198,6 +198,7 @@ struct mpc_handle {
         cudaGraphExec_t exec;
     };
     bool graph_mode = false;
+    std::vector<cudaEvent_t> round_events;  // recorded after each round's polish (mpc_set_round_events)
     cudaStream_t capture_stream = nullptr;
     std::vector<SolveGraph> graphs;
     int64_t graph_captures = 0, graph_replays = 0;
@@ -557,6 +558,9 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
         return cuda_fail(h, e, "cudaMemsetAsync");
     if ((e = cudaMemsetAsync(h->flags, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");
+    // every instance reads MPC_RUNNING (-1) until the round that finishes it
+    if ((e = cudaMemsetAsync(h->out_status, 0xff, (size_t)B * sizeof(int), st)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMemsetAsync");
     // per-stage factors and input checks for the whole batch
     {
         FactorArgs fa{};
@@ -600,6 +604,9 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
             return cuda_fail(h, e, "round kernel launch");
         if ((e = timed_launch(h, kClassPolish, st, [&] { h->shape.launch_polish(r, polish_grid, polish_smem, st); })) != cudaSuccess)
             return cuda_fail(h, e, "polish kernel launch");
+        if (round < (int)h->round_events.size() && h->round_events[round] &&
+            (e = cudaEventRecord(h->round_events[round], st)) != cudaSuccess)
+            return cuda_fail(h, e, "cudaEventRecord");
         if (m1 >= c.max_iter) break;
         m0 = m1;
     }
@@ -794,6 +801,16 @@ mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx,
 static void drop_graphs(mpc_handle* h) {
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+}
+
+mpc_status mpc_set_round_events(mpc_handle* h, void* const* events, int32_t n) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (n < 0 || n > 64 || (n > 0 && !events)) return fail(h, MPC_ERR_INVALID_ARG, "n=%d outside [0, 64] or null events", n);
+    h->round_events.assign(n, nullptr);
+    for (int i = 0; i < n; ++i) h->round_events[i] = static_cast<cudaEvent_t>(events[i]);
+    cudaSetDevice(h->cfg.device);
+    drop_graphs(h);  // captured solves hold the previous events
+    return MPC_OK;
 }
 
 mpc_status mpc_set_graph_mode(mpc_handle* h, int32_t enable) {

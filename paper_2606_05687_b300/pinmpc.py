@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libpinmpc.so")
 
 MPC_OK, MPC_ERR_INVALID_ARG, MPC_ERR_OOM, MPC_ERR_CUDA, MPC_ERR_STATE, MPC_ERR_UNSUPPORTED = range(6)
 CONVERGED, MAX_ITER, NONFINITE, BAD_SET, TIMEOUT, BAD_HORIZON = range(6)
+RUNNING = -1  # status of an instance whose solve has not finished it yet
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID_ARG", 2: "MPC_ERR_OOM", 3: "MPC_ERR_CUDA",
                 4: "MPC_ERR_STATE", 5: "MPC_ERR_UNSUPPORTED"}
 
@@ -81,6 +82,8 @@ def load() -> ctypes.CDLL:
     lib.mpc_load_state.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.c_void_p]
     lib.mpc_load_state.restype = ctypes.c_int
+    lib.mpc_set_round_events.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+    lib.mpc_set_round_events.restype = ctypes.c_int
     lib.mpc_set_graph_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_graph_mode.restype = ctypes.c_int
     lib.mpc_get_graph_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -208,6 +211,14 @@ class Solver:
         self._check(self.lib.mpc_load_state(self.h, _ptr(store), _ptr(idx), store.shape[0], B, _stream_ptr(stream)),
                     "mpc_load_state")
 
+    def set_round_events(self, events):
+        """Record each of `events` (torch.cuda.Event, already created by a record,
+        or raw cudaEvent_t handles) after the matching round of every later solve."""
+        raw = [e.cuda_event if hasattr(e, "cuda_event") else int(e) for e in events]
+        arr = (ctypes.c_void_p * max(len(raw), 1))(*raw)
+        self._check(self.lib.mpc_set_round_events(self.h, arr, len(raw)), "mpc_set_round_events")
+        self._round_events = list(events)
+
     def set_graph_mode(self, enable: bool):
         self._check(self.lib.mpc_set_graph_mode(self.h, 1 if enable else 0), "mpc_set_graph_mode")
 
@@ -270,6 +281,23 @@ def device_inputs(batch, device="cuda", pin_host=False):
     for k, t in out.items():
         out[k] = t.pin_memory() if pin_host else t.to(device)
     return out
+
+
+def round_schedule(cfg: MpcConfig) -> list:
+    """The iteration at which each round of a solve ends (its certificate
+    check): check_start, then intervals starting at check_every, each
+    check_growth times the previous, capped at max_iter."""
+    ends, m0, interval = [], 0, float(cfg.check_every)
+    while True:
+        if m0 == 0:
+            m1 = min(cfg.check_start, cfg.max_iter)
+        else:
+            m1 = int(min(m0 + interval, cfg.max_iter))
+            interval *= cfg.check_growth
+        ends.append(m1)
+        if m1 >= cfg.max_iter:
+            return ends
+        m0 = m1
 
 
 def solver_for(batch, **overrides) -> Solver:

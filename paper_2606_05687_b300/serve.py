@@ -9,7 +9,12 @@ get_traj there; a CUDA event marks the batch done.  Several handles keep
 several batches in flight, so a batch forms while others run.  Each
 request's latency runs from its arrival to the host observing its batch's
 event.  Requests are kept in arrays (a batch is a contiguous run of the
-queue), so the host loop costs per batch, not per request.
+queue), so the host loop costs per batch, not per request.  With
+`early` (the default), a request is answered when the round that certifies
+its instance ends, not when its whole batch does: the library records an
+event after each round (mpc_set_round_events), a side stream copies the
+batch's statuses after it, and the requests whose status is final by then
+are retired; the batch's last event retires the rest.
 
 Every instance of a batch is solved independently, so a request's result
 does not depend on which other requests share its batch (the tests check
@@ -46,7 +51,7 @@ class BatchServer:
 
     def __init__(self, pool: Dict[str, "object"], nx: int, nc: int, contact_dim: int, B_max: int, N: int,
                  n_handles: int = 2, clock: Callable[[], float] = time.perf_counter,
-                 warm_shift: Optional[int] = None, **overrides):
+                 warm_shift: Optional[int] = None, early: bool = True, **overrides):
         import torch
         self.torch = torch
         self.pool = pool
@@ -64,8 +69,20 @@ class BatchServer:
                         status=torch.empty(B_max, dtype=torch.int32, device=self.device),
                         kkt=torch.empty(B_max, dtype=torch.float32, device=self.device))
             status_host = torch.empty(B_max, dtype=torch.int32).pin_memory()
-            self.handles.append(dict(solver=solver, stream=torch.cuda.Stream(self.device), inputs=inputs,
-                                     outs=outs, status_host=status_host, busy=None, event=None, perm=None))
+            h = dict(solver=solver, stream=torch.cuda.Stream(self.device), inputs=inputs,
+                     outs=outs, status_host=status_host, busy=None, event=None, perm=None)
+            if early:
+                n_rounds = len(pinmpc.round_schedule(cfg))
+                side = torch.cuda.Stream(self.device)
+                round_events = [torch.cuda.Event() for _ in range(n_rounds)]
+                for ev in round_events:
+                    ev.record(side)  # creates the event objects
+                solver.set_round_events(round_events)
+                h.update(side=side, round_events=round_events,
+                         round_status=[torch.empty(B_max, dtype=torch.int32).pin_memory() for _ in range(n_rounds)],
+                         round_copied=[torch.cuda.Event() for _ in range(n_rounds)], next_round=0, answered=None)
+            self.handles.append(h)
+        self.early = early
         self.warm_shift = warm_shift
         self.warm_loads = 0
         if warm_shift is not None:
@@ -148,6 +165,14 @@ class BatchServer:
             self.has_state[envs] = True
             h["idx_keep"] = idx
         o = h["outs"]
+        if self.early:
+            # after each round: that round's statuses into pinned memory on the side stream
+            for r, ev in enumerate(h["round_events"]):
+                h["side"].wait_event(ev)
+                s.get_traj(status=h["round_status"][r], stream=h["side"])
+                h["round_copied"][r].record(h["side"])
+            h["next_round"] = 0
+            h["answered"] = np.zeros(B, dtype=bool)
         s.get_traj(xi=o["xi"], u=o["u"], status=o["status"], kkt=o["kkt"], stream=h["stream"])
         with torch.cuda.stream(h["stream"]):
             h["status_host"][:B].copy_(o["status"][:B], non_blocking=True)
@@ -156,11 +181,28 @@ class BatchServer:
         h["busy"], h["event"], h["perm"] = (lo, hi), ev, perm
         self.batches += 1
 
+    def _answer_early(self, h, now):
+        """Retire the requests whose instances the rounds copied so far finished."""
+        lo, hi = h["busy"]
+        order = h["perm"] if h["perm"] is not None else np.arange(hi - lo)
+        while h["next_round"] < len(h["round_events"]) and h["round_copied"][h["next_round"]].query():
+            st = h["round_status"][h["next_round"]][:hi - lo].numpy()
+            new = (st != pinmpc.RUNNING) & ~h["answered"]
+            if new.any():
+                now = self.clock() if now is None else now
+                req = lo + order[new]
+                self.t_done[req] = now
+                self.status[req] = st[new]
+                h["answered"] |= new
+            h["next_round"] += 1
+        return now
+
     def _retire(self, h, now):
         lo, hi = h["busy"]
         # slot i holds request lo + order[i]
         order = h["perm"] if h["perm"] is not None else np.arange(hi - lo)
-        self.t_done[lo:hi] = now
+        late = ~h["answered"] if self.early else np.ones(hi - lo, dtype=bool)
+        self.t_done[lo + order[late]] = now
         self.status[lo + order] = h["status_host"][:hi - lo].numpy()
         if self.keep_results:
             o = {k: h["outs"][k][:hi - lo].cpu().numpy() for k in ("u", "xi", "kkt")}
@@ -172,7 +214,13 @@ class BatchServer:
         """One pass of the serving loop: retire finished batches, start new ones."""
         now = None
         for h in self.handles:
-            if h["busy"] is not None and h["event"].query():
+            if h["busy"] is None:
+                continue
+            if self.early:
+                now = self._answer_early(h, now)
+                if h["next_round"] < len(h["round_events"]):
+                    continue  # the side stream still copies this batch's statuses
+            if h["event"].query():
                 now = self.clock() if now is None else now
                 self._retire(h, now)
         for h in self.handles:

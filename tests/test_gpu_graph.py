@@ -63,3 +63,37 @@ def test_graph_replay_with_warm_start_and_timing(P):
     assert same(P.solve_workload(batch, solver=ref), P.solve_workload(batch, solver=s))
     ref.close()
     s.close()
+
+
+def test_round_events_expose_finished_instances(P):
+    # after round r's event, an instance reads its final status exactly when its
+    # certified iteration count is at most the round's end, else MPC_RUNNING
+    import torch
+    batch = W.generate(W.rl_scale_walking(B=512, N=20, seed=55))
+    s = P.solver_for(batch)
+    ends = P.round_schedule(s.cfg)
+    side = torch.cuda.Stream()
+    events = [torch.cuda.Event() for _ in ends]
+    for ev in events:
+        ev.record(side)
+    s.set_round_events(events)
+    main = torch.cuda.current_stream()
+    s.set_stages(batch.B, batch.N, **P.device_inputs(batch), stream=main)
+    s.solve(batch.B, stream=main)
+    per_round = [torch.empty(batch.B, dtype=torch.int32, device="cuda") for _ in ends]
+    for ev, st in zip(events, per_round):
+        side.wait_event(ev)
+        s.get_traj(status=st, stream=side)
+    final = torch.empty(batch.B, dtype=torch.int32, device="cuda")
+    iters = torch.empty(batch.B, dtype=torch.int32, device="cuda")
+    s.get_traj(status=final, iters=iters, stream=main)
+    torch.cuda.synchronize()
+    final, iters = final.cpu().numpy(), iters.cpu().numpy()
+    assert np.all(final == P.CONVERGED) and iters.max() > ends[0]  # some instances need a later round
+    for end, st in zip(ends, per_round):
+        st = st.cpu().numpy()
+        done = iters <= end
+        assert np.array_equal(st[done], final[done]) and np.all(st[~done] == P.RUNNING), end
+    assert np.array_equal(P.solve_workload(batch)["status"], final)
+    s.set_round_events([])
+    s.close()
