@@ -88,7 +88,9 @@ typedef struct mpc_config {
     int32_t accel;         /* 1: fast ADMM with restart; 0: plain ADMM */
     float restart_eta;     /* restart threshold eta in (0, 1) */
     int32_t refine_steps;  /* after a failed polish: up to this many active-set updates, each
-                              reading the faces off Proj(u - refine_alpha * grad) and polishing again */
+                              reading the faces off Proj(u - refine_alpha * grad) and polishing again;
+                              in the first two rounds -- each later round doubles it, up to 32, for
+                              the few instances still running */
     float refine_alpha;    /* step of that projected-gradient active-set update (scaled units) */
     float foot_half_length;/* d_x of the wrench cone (contact_dim 6) */
     float foot_half_width; /* d_y of the wrench cone (contact_dim 6) */

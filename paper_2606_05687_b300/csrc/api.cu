@@ -597,6 +597,9 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
         r.cnt_out = cnt + out;
         r.cursor = cursor;
         r.warm_B = (h->warm_N == h->N_set) ? std::min(h->warm_B, B) : 0;
+        // the few instances left after two rounds get more refinement: the
+        // allowance doubles per round from round 2 on (up to 32)
+        r.refine_steps = std::min(32, c.refine_steps << std::min(std::max(round - 1, 0), 4));
         if ((e = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(cnt + out, 0, sizeof(int), st)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemsetAsync");
