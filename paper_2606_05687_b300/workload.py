@@ -61,6 +61,7 @@ class WorkloadSpec:
     u_prev_scale: float = 0.0     # std of u_{-1} (the velocity-form initial input)
     ref_noise: float = 0.1        # std of the reference / initial-state noise
     model: str = "srb13"          # "srb13": 13-state convex model; "cd9": the 9-state centroidal model
+    horizon_min: int = 0          # > 0: per-instance horizons uniform in horizon_min .. N (stage stride N)
 
     @property
     def nu(self) -> int:
@@ -80,6 +81,16 @@ def rl_scale_walking(B: int = 4096, N: int = 20, seed: int = 1002, **kw) -> Work
     return WorkloadSpec(B=B, N=N, contact_dim=3, n_contacts=8, seed=seed,
                         schedule=kw.pop("schedule", "walking"),
                         f_max=kw.pop("f_max", 375.0), **kw)
+
+
+def uneven_mixed(B: int = 16384, N: int = 32, seed: int = 1003, **kw) -> list:
+    """Uneven batching: half the environments with eight 3-D contact points and
+    a walking gait, half with two 6-D foot wrenches and Bernoulli stance;
+    horizons uniform in 5 .. N per environment (stage stride N).  Two specs,
+    one per contact model (each model is its own solver shape)."""
+    n1 = B // 2
+    return [rl_scale_walking(B=n1, N=N, seed=seed, horizon_min=5, **kw),
+            small_centroidal(B=B - n1, N=N, seed=seed + 1, horizon_min=5, **kw)]
 
 
 def centroidal9_walking(B: int = 4096, N: int = 20, seed: int = 1004, **kw) -> WorkloadSpec:
@@ -217,6 +228,8 @@ def _draw_instance(spec: WorkloadSpec, b: int) -> dict:
     d["phase"] = rng.uniform(0.0, 1.0)
     d["e_noise"] = rng.normal(0.0, 1.0, size=(N, NX))
     d["u_prev_noise"] = rng.normal(0.0, 1.0, size=nu)
+    # drawn last, so the draws above do not depend on it
+    d["horizon"] = int(rng.integers(spec.horizon_min, N + 1)) if spec.horizon_min > 0 else N
     return d
 
 
@@ -324,7 +337,7 @@ def generate(spec: WorkloadSpec, instances: Optional[Sequence[int]] = None) -> B
     out = Batch(spec=dataclasses.replace(spec, B=nb), A=f32(A), Bm=f32(Bm), e=f32(e),
                 Q=f32(Q), R=f32(R), ry=f32(ry), ru=f32(ru), mu=f32(mu), fmax=f32(fmax),
                 mask=mask, xi0=f32(xi0), u_prev=f32(u_prev),
-                horizon=np.full(nb, N, dtype=np.int32),
+                horizon=np.asarray([d["horizon"] for d in draws], dtype=np.int32),
                 nu_arr=np.full(nb, nu, dtype=np.int32))
     if nominal is not None:
         out.nominal = nominal  # linearisation point of the cd9 model (float64), for checks

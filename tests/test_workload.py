@@ -87,3 +87,14 @@ def test_cd9_linearisation_against_the_centroidal_dynamics():
                     got = lin.copy()
                     got[6:9] -= want
                     assert np.allclose(got, nonlin, rtol=0, atol=1e-4 * (1 + np.abs(nonlin).max())), (spec.contact_dim, i, k)
+
+
+def test_per_instance_horizons_leave_other_draws_unchanged():
+    a = W.generate(W.rl_scale_walking(B=64))
+    b = W.generate(W.rl_scale_walking(B=64, horizon_min=5))
+    assert np.all(a.horizon == 20) and b.horizon.min() >= 5 and b.horizon.max() <= 20 and len(set(b.horizon)) > 8
+    for k in ("A", "Bm", "Q", "R", "ry", "xi0", "mu", "mask", "e"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    assert np.array_equal(W.generate(W.rl_scale_walking(B=64, horizon_min=5), instances=[9, 33]).horizon, b.horizon[[9, 33]])
+    parts = W.uneven_mixed(B=100, N=32)
+    assert [p.B for p in parts] == [50, 50] and {p.contact_dim for p in parts} == {3, 6}
