@@ -514,10 +514,11 @@ def run_gpu(args):
     uneven = None
     if not args.device_only:
         # uneven batching: 16384 environments, half point contacts (walking),
-        # half foot wrenches (Bernoulli stance), horizons uniform in 5 .. 32;
-        # one handle per contact model, both solved concurrently on their streams
+        # half foot wrenches (Bernoulli stance), horizons uniform in 5 .. 40
+        # (above 32 stages the ADMM rounds run as CTA pairs); one handle per
+        # contact model, both solved concurrently on their streams
         from paper_2606_05687_b300.mixed import MixedSolver
-        parts = [W.generate(sp) for sp in W.uneven_mixed(B=16384, N=32, seed=SEED + 1)]
+        parts = [W.generate(sp) for sp in W.uneven_mixed(B=16384, N=40, seed=SEED + 1)]
         ms = MixedSolver(parts, max_iter=args.max_iter)
         ms.set_stages([pinmpc.device_inputs(p_, "cuda") for p_ in parts])
         ms.solve()
@@ -536,7 +537,7 @@ def run_gpu(args):
                   "ms_per_solve": umt * 1e3,
                   "iters_mean": [float(r_["iters"].mean()) for r_ in res_],
                   "workload": "16384 envs: 8192 walking (8 point contacts) + 8192 Bernoulli-stance (2 foot wrenches), "
-                              "horizons U{5..32}, stage stride 32, both shapes solved concurrently (inputs resident)"}
+                              "horizons U{5..40}, stage stride 40, both shapes solved concurrently (inputs resident)"}
 
     if rank != 0:
         return

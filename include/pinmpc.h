@@ -133,9 +133,11 @@ typedef struct mpc_handle mpc_handle;
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,
                               int32_t contact_dim, int32_t B_max, int32_t N_max);
 
-/* Largest horizon N_max that mpc_create accepts for (nx, nu): 32 (one warp
- * per stage) for both built shapes; 0 if the shape is not built.
- * mpc_solve_noalloc has a lower limit of its own for nu = 24 (below). */
+/* Largest horizon N_max that mpc_create accepts for (nx, nu): 64 for both
+ * built shapes (one warp per stage; above 32 stages each ADMM round runs as a
+ * thread-block cluster of two CTAs per instance, half of the stages in each);
+ * 0 if the shape is not built.  mpc_solve_noalloc has a lower limit of its
+ * own (below). */
 int32_t mpc_max_horizon(int32_t nx, int32_t nu);
 
 /* Validate cfg, select its device and allocate the workspace (owned by the

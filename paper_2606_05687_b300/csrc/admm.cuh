@@ -155,6 +155,12 @@ struct RCtx {
     float *var, *xb, *tmp, *pre, *fac, *part;
     int N, Nh;
     float rho;
+    // two-CTA form: this CTA holds global stages [k0, k0 + nloc) at local
+    // indices 0..nloc-1; pvar/pxb are the other CTA's var/xb (generic
+    // addresses into its shared memory) and pjl the local index there of
+    // global stage k0 - 1
+    const float *pvar, *pxb;
+    int k0, nloc, pjl;
     __device__ float* T(int j, int t) const { return tmp + (j * RoundSmem<D>::kTmp + t) * D::NBP; }
     __device__ const float* P(int j, int t) const { return pre + (j * 3 + t) * D::NBP; }
     // padded row min(lane/2, NX-1) of S_j (m = 0) or W_j (m = 1)
@@ -212,7 +218,7 @@ __device__ __forceinline__ void load_hats(const RCtx<D>& c, StageRegs<D>& R, int
 
 // Block 1 of stage j (warp j): du_j, xibar_j = H_{j-1} htilde_{j-1} (factored),
 // Abar_j xibar_j, and xibar_N for the last stage.
-template <class D>
+template <class D, bool CL = false>
 __device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, StageRegs<D>& R, int cb, int j,
                                          int lane, float wa, float wb) {
     constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP;
@@ -248,11 +254,17 @@ __device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, Sta
     const float sx = __shfl_sync(0xffffffffu, sr, (2 * lane) & 31);
     R.bd[0] = lane < NX ? sx : g0 - bs.x;
     R.bd[1] = g1 - bs.y;
-    if (j >= 1) {
+    // global stage index (j itself except in the two-CTA form)
+    const int jg = CL ? c.k0 + j : j;
+    if (jg >= 1) {
         // w = zhat_j - vhat_j - ebar_j + lambdahat_j ;
         // c' = D'^{-1}(qbar + rho (zhat_{j-1} - thetahat_{j-1}) + rho [0; w_u])
-        const float* cur = c.var + RoundState<D>::at(c.N, cb, j - 1, 0);
-        const float* prv = c.var + RoundState<D>::at(c.N, 1 - cb, j - 1, 0);
+        // (stage j-1 of the first local stage lives in the other CTA)
+        const bool remote = CL && j == 0;
+        const float* vb = remote ? c.pvar : c.var;
+        const int jp = remote ? c.pjl : j - 1;
+        const float* cur = vb + RoundState<D>::at(c.N, cb, jp, 0);
+        const float* prv = vb + RoundState<D>::at(c.N, 1 - cb, jp, 0);
         const float w0 = R.zh[0] - R.vh[0] - R.e0 + R.lah[0];
         float cc0 = 0.0f, cc1 = 0.0f;
         if (v0) {
@@ -292,8 +304,8 @@ __device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, Sta
         R.ax[0] = lane < NX ? axs : xb0;
         R.ax[1] = xb1;
     }
-    if (j == c.Nh - 1) {
-        float* xbN = c.xb + c.Nh * NBP;
+    if (jg == c.Nh - 1) {
+        float* xbN = c.xb + (CL ? j + 1 : c.Nh) * NBP;
         const float* qb = c.P(j, PQB);
         const float* idn = c.P(j, PIDN);
         xbN[lane] = v0 ? fmaf(rho, R.zh[0] - R.thh[0], qb[lane]) * idn[lane] : 0.0f;
@@ -303,13 +315,15 @@ __device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, Sta
 
 // Block 2 and the dual ascents of stage j; new values go to buffer 1 - cb.
 // Returns the stage's share of the combined residual (valid in every lane).
-template <class D>
+template <class D, bool CL = false>
 __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int cb, int j, int lane, float dx,
                                           float dy) {
     constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP, CD = D::CD;
     constexpr bool TWO = RegT<D>::kTwo;
     const bool v0 = lane < NB, v1 = TWO && lane < NB - 32;
-    const float* xbn = c.xb + (j + 1) * NBP;
+    // xibar_{j+1} of the last local stage comes from the other CTA's first
+    // stage unless j is the last stage of the horizon
+    const float* xbn = (CL && j + 1 == c.nloc && c.k0 + j + 1 < c.Nh) ? c.pxb : c.xb + (j + 1) * NBP;
     float* arg = c.T(j, 0);
     float* zp = c.T(j, 1);
     // gamma = B du + betahat - Abar xibar - ebar + lambdahat ; gammatilde = xibar_{j+1} + thetahat + Abar xibar + ebar - lambdahat

@@ -12,6 +12,7 @@
 #include "../../include/pinmpc.h"
 #include "admm.cuh"
 #include "polish_cta.cuh"
+#include "round_cluster.cuh"
 #include "internal.h"
 #include "warm_state.cuh"
 
@@ -54,8 +55,9 @@ template <class D>
 int polish_smem_t(int N) { return CtaSmem<D>(N).total * 4; }
 template <class D>
 int state_floats_t(int N) { return RoundState<D>::floats(N); }
+// above 32 stages the round runs as CTA pairs, each holding ceil(N/2) stages
 template <class D>
-int round_smem_t(int N, bool dbl) { return RoundSmem<D>(N, dbl).bytes(); }
+int round_smem_t(int N, bool dbl) { return N > 32 ? RoundSmem<D>((N + 1) / 2, false).bytes() : RoundSmem<D>(N, dbl).bytes(); }
 template <class D>
 int cache_floats_t(int N) { return RoundSmem<D>::cache_floats(N); }
 template <class D>
@@ -69,13 +71,25 @@ cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(round2_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(round_cl_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(round_cl_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(polish_cta_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
 }
 template <class D>
 void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
-    // register-heavy form for up to 20 stages (640 threads), 64-register form above
-    if (a.N <= 20) round2_kernel<D, 640><<<B, 32 * a.N, smem, s>>>(a);
-    else round2_kernel<D, 1024><<<B, 32 * a.N, smem, s>>>(a);
+    // register-heavy form for up to 20 stages per CTA (640 threads), 64-register
+    // form above; B persistent workers: CTAs, or CTA pairs above 32 stages
+    if (a.N > 32) {
+        const int nl = (a.N + 1) / 2;
+        if (nl <= 20) round_cl_kernel<D, 640><<<2 * B, 32 * nl, smem, s>>>(a);
+        else round_cl_kernel<D, 1024><<<2 * B, 32 * nl, smem, s>>>(a);
+    } else if (a.N <= 20) {
+        round2_kernel<D, 640><<<B, 32 * a.N, smem, s>>>(a);
+    } else {
+        round2_kernel<D, 1024><<<B, 32 * a.N, smem, s>>>(a);
+    }
 }
 template <class D>
 void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
@@ -85,7 +99,10 @@ template <class D>
 int resident_per_sm_t(int kernel, int N, int smem) {
     int n = 0;
     cudaError_t e;
-    if (kernel == 0) {
+    if (kernel == 0 && N > 32) {
+        // one CTA of a pair per SM: its shared memory is above half an SM's
+        return 1;
+    } else if (kernel == 0) {
         if (N <= 20) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, round2_kernel<D, 640>, 32 * N, smem);
         else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, round2_kernel<D, 1024>, 32 * N, smem);
     } else {
@@ -358,9 +375,10 @@ int32_t mpc_max_horizon(int32_t nx, int32_t nu) {
     Shape sh;
     const int cd = (nu == 24) ? 3 : 6;
     if (nu % cd != 0 || !pick_shape(nx, nu / cd, cd, &sh)) return 0;
-    // one warp per stage (32 stages at most) and each kernel's shared memory
+    // one warp per stage (32 stages per CTA, CTA pairs above 32) and each
+    // kernel's shared memory
     int best = 0;
-    for (int N = 1; N <= 32; ++N)
+    for (int N = 1; N <= kClusterMaxN; ++N)
         if (sh.round_smem(N, false) <= kSmemLimit && sh.polish_smem(N) <= kSmemLimit) best = N;
     return best;
 }
@@ -383,8 +401,9 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
         !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f) || c.refine_steps < 0 ||
         !(c.refine_alpha > 0.0f))
         return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
-    if (c.N_max > 32)
-        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds 32 stages (one warp per stage)", c.N_max);
+    if (c.N_max > kClusterMaxN)
+        return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds %d stages (one warp per stage, two CTAs)",
+                    c.N_max, kClusterMaxN);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess) {
@@ -576,7 +595,9 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
     // left costs one short launch of each kernel
     int* cursor = h->work;
     int* cnt = h->work + 2;
-    const int round_grid = std::max(1, std::min(B, h->sms * h->shape.resident_per_sm(0, h->N_set, round_smem)));
+    // persistent workers: CTAs, or CTA pairs (two SMs each) above 32 stages
+    const int round_grid = std::max(
+        1, std::min(B, h->sms * h->shape.resident_per_sm(0, h->N_set, round_smem) / (h->N_set > 32 ? 2 : 1)));
     const int polish_grid = B;
     int m0 = 0, round = 0;
     double interval = c.check_every;
@@ -636,7 +657,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
     // double-buffered records and factors (TMA prefetch) when they fit
     const int smem_single = h->shape.round_smem(h->N_set, false), smem_dbl = h->shape.round_smem(h->N_set, true);
-    const bool dbl = smem_dbl <= h->optin_smem;
+    const bool dbl = h->N_set <= 32 && smem_dbl <= h->optin_smem;
     const int round_smem = dbl ? smem_dbl : smem_single;
     if (round_smem > h->round_attr) {
         if ((e = h->shape.set_round_attrs(round_smem, h->shape.polish_smem(c.N_max))) != cudaSuccess)

@@ -83,7 +83,7 @@ def rl_scale_walking(B: int = 4096, N: int = 20, seed: int = 1002, **kw) -> Work
                         f_max=kw.pop("f_max", 375.0), **kw)
 
 
-def uneven_mixed(B: int = 16384, N: int = 32, seed: int = 1003, **kw) -> list:
+def uneven_mixed(B: int = 16384, N: int = 40, seed: int = 1003, **kw) -> list:
     """Uneven batching: half the environments with eight 3-D contact points and
     a walking gait, half with two 6-D foot wrenches and Bernoulli stance;
     horizons uniform in 5 .. N per environment (stage stride N).  Two specs,

@@ -61,8 +61,8 @@ def test_defaults_and_limits(P):
     assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(2e-6)
     assert cfg.polish == 1 and cfg.accel == 1
     lib = P.load()
-    assert lib.mpc_max_horizon(13, 24) == 32  # one warp per stage
-    assert lib.mpc_max_horizon(13, 12) == 32
+    assert lib.mpc_max_horizon(13, 24) == 64  # one warp per stage, two CTAs above 32
+    assert lib.mpc_max_horizon(13, 12) == 64
     assert lib.mpc_max_horizon(13, 7) == 0
 
 
@@ -74,6 +74,8 @@ def test_argument_errors_without_device(P):
     assert b"contact_dim" in lib.mpc_last_error(None)
     unsup = P.default_config(12, 8, 3, 16, 20)
     assert lib.mpc_create(ctypes.byref(unsup), ctypes.byref(h)) == P.MPC_ERR_UNSUPPORTED
+    too_long = P.default_config(13, 8, 3, 16, 65)
+    assert lib.mpc_create(ctypes.byref(too_long), ctypes.byref(h)) == P.MPC_ERR_UNSUPPORTED
     neg = P.default_config(13, 8, 3, 16, 20, rho=-1.0)
     assert lib.mpc_create(ctypes.byref(neg), ctypes.byref(h)) == P.MPC_ERR_INVALID_ARG
     assert lib.mpc_set_stages(None, None, None) == P.MPC_ERR_INVALID_ARG

@@ -1,0 +1,87 @@
+"""Horizons above 32 stages: the ADMM round runs as a thread-block cluster
+of two CTAs per instance, half of the stages in each.  Parity with the
+oracle for ragged horizons U{5..40}, for the edge horizons 1, 2, 3, 33, 63
+and 64 of a 64-stage batch (one CTA of the pair empty; the 640- and the
+1024-thread forms), a warm restart at 40 stages, and instances of 32 stages
+or fewer, which a 32-stage handle solves with the one-CTA form."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2606_05687_b300 import workload as W
+
+from parity_util import REL_TRAJ, compare, oracle_refs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pinmpc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05687_b300 import pinmpc as P
+    return P
+
+
+def _first_stages(batch, n):
+    """The batch cut to its first n stages (horizons must be n or fewer)."""
+    assert int(batch.horizon.max()) <= n
+    kw = {}
+    for f in dataclasses.fields(batch):
+        v = getattr(batch, f.name)
+        kw[f.name] = v if f.name in ("spec", "xi0", "u_prev", "horizon", "nu_arr") else np.ascontiguousarray(v[:, :n])
+    kw["spec"] = dataclasses.replace(batch.spec, N=n)
+    return W.Batch(**kw)
+
+
+def test_max_horizon_reports_pairs(pinmpc):
+    lib = pinmpc.load()
+    assert lib.mpc_max_horizon(13, 24) == 64 and lib.mpc_max_horizon(13, 12) == 64
+
+
+def test_ragged_horizons_up_to_40(pinmpc):
+    batch = W.generate(W.rl_scale_walking(B=128, N=40, seed=81, horizon_min=5))
+    out = pinmpc.solve_workload(batch)
+    assert np.all(out["status"] == 0), np.flatnonzero(out["status"])
+    h = batch.horizon
+    ids = [int(np.argmin(h)), int(np.argmax(h))] + [int(i) for i in np.flatnonzero(h == 33)[:1]]
+    ids += [int(i) for i in np.flatnonzero((h > 32) & (h < 40))[:3]] + [int(i) for i in np.flatnonzero(h <= 32)[:2]]
+    compare(batch, out, ids)
+    # instances of 32 stages or fewer: the same solution from a 32-stage
+    # handle, which runs the one-CTA form
+    short = [int(i) for i in np.flatnonzero(h <= 32)[:8]]
+    sub = _first_stages(batch.subset(short), 32)
+    one = pinmpc.solve_workload(sub)
+    assert np.all(one["status"] == 0)
+    for t, b in enumerate(short):
+        n = int(h[b])
+        su = np.abs(out["u"][b, :n]).max()
+        assert np.abs(one["u"][t, :n] - out["u"][b, :n]).max() <= 2 * REL_TRAJ * su
+
+
+def test_edge_horizons_64(pinmpc):
+    batch = W.generate(W.small_centroidal(B=16, N=64, seed=83))
+    batch.horizon[:6] = [1, 2, 3, 33, 63, 64]
+    out = pinmpc.solve_workload(batch)
+    ids = list(range(6))
+    compare(batch, out, ids)
+    # shorter horizons leave the outputs past them zero
+    assert np.all(out["u"][0, 1:] == 0) and np.all(out["xi"][3, 33:] == 0)
+
+
+def test_warm_restart_40(pinmpc):
+    batch = W.generate(W.rl_scale_walking(B=64, N=40, seed=85))
+    s = pinmpc.solver_for(batch)
+    cold = pinmpc.solve_workload(batch, solver=s)
+    s.warm_start(0)
+    warm = pinmpc.solve_workload(batch, solver=s)
+    assert np.all(cold["status"] == 0) and np.all(warm["status"] == 0)
+    assert warm["iters"].max() <= s.cfg.check_start
+    ids = [0, 21, 63]
+    refs = oracle_refs(batch, ids)
+    compare(batch, cold, ids, refs)
+    compare(batch, warm, ids, refs)

@@ -19,8 +19,8 @@ def test_mixed_shapes_and_ragged_horizons():
     __graft_entry__.build()
     from paper_2606_05687_b300 import pinmpc
     from paper_2606_05687_b300.mixed import MixedSolver
-    batches = [W.generate(sp) for sp in W.uneven_mixed(B=256, N=32, seed=71)]
-    assert batches[0].horizon.min() >= 5 and batches[0].horizon.max() <= 32 and len(set(batches[0].horizon)) > 10
+    batches = [W.generate(sp) for sp in W.uneven_mixed(B=256, N=40, seed=71)]
+    assert batches[0].horizon.min() >= 5 and batches[0].horizon.max() <= 40 and len(set(batches[0].horizon)) > 10
     ms = MixedSolver(batches)
     ms.set_stages([pinmpc.device_inputs(b) for b in batches])
     ms.solve()
