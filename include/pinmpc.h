@@ -126,10 +126,12 @@ typedef struct mpc_handle mpc_handle;
  * can reach ~30x that residual -- checks at iterations 12, 32, 72, 152, ...
  * (check_start 12, check_every 20, check_growth 2), polish on with up to 3
  * refinement steps of alpha 0.01, acceleration on with eta 0.999, foot
- * 0.10 x 0.05 m).  The check schedule and the refinement step are this
- * implementation's choices (the paper checks convergence every iteration and
- * has no polish); they were chosen by measured throughput on the walking and
- * small centroidal workloads. */
+ * 0.10 x 0.05 m).  For foot wrenches (contact_dim 6) on the 13-state model:
+ * rho 300, check_start 32 (checks at 32, 52, 92, ...), up to 4 refinement
+ * steps of alpha 0.001.  The check schedule, the refinement step and rho are
+ * this implementation's choices (the paper checks convergence every
+ * iteration and has no polish); they were chosen by measured throughput on
+ * the walking and small centroidal workloads of each shape. */
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts,
                               int32_t contact_dim, int32_t B_max, int32_t N_max);
 

@@ -33,3 +33,13 @@ def test_library_defaults_match_the_c_defaults():
     cfg = pinmpc.default_config(13, 8, 3, 16, 20)
     for k, v in A.LIBRARY_DEFAULTS.items():
         assert abs(getattr(cfg, k) - v) < 1e-9, k
+    assert A.library_defaults(13, 8, 3) == A.LIBRARY_DEFAULTS
+    # each shape's defaults are a point of the default grid, and the search
+    # for that shape starts there
+    for shape in ((13, 8, 3), (13, 2, 6), (9, 8, 3), (9, 2, 6)):
+        d = A.library_defaults(*shape)
+        assert all(d[k] in A.DEFAULT_GRID[k] for k in d), (shape, d)
+        assert A.candidates(limit=1, defaults=d)[0] == d
+    assert A.library_defaults(13, 2, 6) == {"check_start": 32, "check_every": 20, "refine_alpha": 0.001,
+                                            "rho": 300.0, "refine_steps": 4}
+    assert A.library_defaults(9, 2, 6) == A.LIBRARY_DEFAULTS

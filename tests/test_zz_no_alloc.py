@@ -69,7 +69,7 @@ def test_no_alloc_rejects_batches_beyond_its_scratch(P):
 
 def test_no_alloc_rejects_horizons_beyond_its_kernel(P):
     # its single kernel holds a whole instance in shared memory: 24 stages at
-    # most for point contacts (nu = 24), while the handle path takes 32
+    # most for point contacts (nu = 24), while the handle path takes 64
     import torch
     batch = W.generate(W.rl_scale_walking(B=4, N=25, seed=2027))
     with pytest.raises(P.MpcError) as ei:
