@@ -511,6 +511,37 @@ def run_gpu(args):
         graph = dict(res, what="host time to enqueue one solve of B (median), and the wall-clock latency of a 64-environment "
                                "set_stages/solve/get_traj round trip (median), direct launches vs one CUDA-graph launch")
 
+    fleet = None
+    if not args.device_only and world == 1:
+        # the serving configuration at fleet scale: 65536 environments, each
+        # a controller ticking at 50 Hz (3.28M requests/s offered, above
+        # capacity), horizons 10 / 20 / 30 per environment (stage stride 30),
+        # episode resets as a Poisson process of 0.5/s per environment, warm
+        # starts (one-stage shift) from each environment's stored state; a tick
+        # that finds its environment's previous request pending is counted
+        # as skipped.  Stage data: 8192 distinct walking instances, tiled 8x
+        # (the horizons are drawn per environment), fixed per environment, so
+        # the shifted warm start is a perturbed guess, not a true receding step
+        from paper_2606_05687_b300.serve import BatchServer, fleet_load
+        n_env, n_dist, nf = 65536, 8192, 30
+        fb = W.generate(W.rl_scale_walking(B=n_dist, N=nf, seed=SEED + 3))
+        ft = pinmpc.device_inputs(fb, "cuda")
+        tile = torch.arange(n_env, device="cuda") % n_dist
+        pool = {k: torch.index_select(v, 0, tile).contiguous() for k, v in ft.items()}
+        rng_h = np.random.default_rng(SEED + 3)
+        pool["horizon"] = torch.from_numpy(rng_h.choice(np.array([10, 20, 30], np.int32), size=n_env)).to("cuda")
+        del ft
+        fsrv = BatchServer(pool, fb.nx, fb.nc, fb.contact_dim, B_max=8192, N=nf, n_handles=SERVE_HANDLES,
+                           warm_shift=1, max_iter=args.max_iter)
+        fleet = fleet_load(fsrv, hz=50.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 3)
+        fleet.update(warm_loads=fsrv.warm_loads, batches=fsrv.batches,
+                     workload="65536 envs x 50 Hz (walking, 8 point contacts), horizons {10,20,30}, stage stride 30, "
+                              "Poisson resets 0.5/s/env, warm shift 1; 8192 distinct instances tiled 8x; "
+                              f"{SERVE_HANDLES} handles of B_max 8192; window 2 s after 0.5 s warm-up")
+        fsrv.close()
+        del pool, fsrv
+        torch.cuda.empty_cache()
+
     uneven = None
     if not args.device_only:
         # uneven batching: 16384 environments, half point contacts (walking),
@@ -570,6 +601,7 @@ def run_gpu(args):
         "landmarks": landmark,
         "graph": graph,
         "uneven": uneven,
+        "fleet": fleet,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),

@@ -268,3 +268,75 @@ def serve_load(server: BatchServer, arrivals: np.ndarray) -> dict:
             "offered_per_s": (hi - lo) / max(float(times[-1]), 1e-9), "achieved_per_s": (hi - lo) / span,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_batch": (hi - lo) / max(server.batches - batches0, 1)}
+
+
+def fleet_load(server, hz: float = 50.0, duration: float = 1.0, warmup: float = 0.0, reset_rate: float = 0.0,
+               seed: int = 0) -> dict:
+    """A fleet of controllers, one per environment of the server's pool, each
+    ticking at `hz` (phases uniform).  At each tick an environment requests
+    the solve of its next MPC step, unless its previous request is still
+    unanswered: then the tick is counted as skipped (the controller keeps its
+    last plan) -- nothing is dropped silently.  Episodes end as a Poisson
+    process of `reset_rate` per environment per second; `server.reset(env)`
+    makes the environment's next request cold.
+
+    Runs for `warmup` + `duration` seconds of the server's clock, then drains.
+    Figures cover the measured window [warmup, warmup + duration): ticks,
+    requests submitted, skipped ticks, requests answered in the window per
+    second, and the latency percentiles (tick to answer) of the requests
+    that arrived in it."""
+    n_env = int(server.pool["A"].shape[0])
+    rng = np.random.default_rng(seed)
+    period = 1.0 / hz
+    next_tick = rng.uniform(0.0, period, n_env)
+    next_reset = rng.exponential(1.0 / reset_rate, n_env) if reset_rate > 0 else np.full(n_env, np.inf)
+    pending = np.full(n_env, -1, np.int64)
+    end = warmup + duration
+    counts = dict(ticks=0, skipped=0, resets=0)
+    t0 = server.clock()
+    first = server.n
+    while True:
+        now = server.clock() - t0
+        if now >= end:
+            break
+        measured = now >= warmup
+        due_r = next_reset <= now
+        if due_r.any():
+            er = np.flatnonzero(due_r)
+            server.reset(er)
+            if measured:
+                counts["resets"] += er.size
+            next_reset[er] += rng.exponential(1.0 / reset_rate, er.size)
+        busy = np.flatnonzero(pending >= 0)
+        if busy.size:
+            answered = ~np.isnan(server.t_done[pending[busy]])
+            pending[busy[answered]] = -1
+        idx = np.flatnonzero(next_tick <= now)
+        if idx.size:
+            nt = np.floor((now - next_tick[idx]) / period).astype(np.int64) + 1  # ticks passed since the last look
+            free = pending[idx] < 0
+            sub = idx[free]
+            if measured:
+                counts["ticks"] += int(nt.sum())
+                counts["skipped"] += int(nt.sum()) - sub.size
+            if sub.size:
+                # each request arrives at its environment's latest tick
+                t_arr = t0 + next_tick[sub] + (nt[free] - 1) * period
+                pending[sub] = np.arange(server.n, server.n + sub.size)
+                server.submit(sub, t_arr)
+            next_tick[idx] += nt * period
+        server.step()
+    server.drain()
+    lo, hi = first, server.n
+    t_arr = server.t_arrival[lo:hi] - t0
+    t_done = server.t_done[lo:hi] - t0
+    win = (t_arr >= warmup) & (t_arr < end)
+    lat = (t_done[win] - t_arr[win]) * 1e3
+    done_in = int(np.sum((t_done >= warmup) & (t_done < end)))
+    return {"envs": n_env, "hz": hz, "window_s": duration,
+            "offered_ticks_per_s": counts["ticks"] / duration,
+            "requests": int(win.sum()), "skipped_ticks": counts["skipped"], "resets": counts["resets"],
+            "answered_per_s": done_in / duration,
+            "certified": int(np.sum(server.status[lo:hi][win] == 0)),
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None}
