@@ -532,12 +532,13 @@ def run_gpu(args):
         pool["horizon"] = torch.from_numpy(rng_h.choice(np.array([10, 20, 30], np.int32), size=n_env)).to("cuda")
         del ft
         fsrv = BatchServer(pool, fb.nx, fb.nc, fb.contact_dim, B_max=8192, N=nf, n_handles=SERVE_HANDLES,
-                           warm_shift=1, max_iter=args.max_iter)
+                           warm_shift=1, horizon_classes=pinmpc.horizon_classes_for(nf), max_iter=args.max_iter)
         fleet = fleet_load(fsrv, hz=50.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 3)
         fleet.update(warm_loads=fsrv.warm_loads, batches=fsrv.batches,
                      workload="65536 envs x 50 Hz (walking, 8 point contacts), horizons {10,20,30}, stage stride 30, "
                               "Poisson resets 0.5/s/env, warm shift 1; 8192 distinct instances tiled 8x; "
-                              f"{SERVE_HANDLES} handles of B_max 8192; window 2 s after 0.5 s warm-up")
+                              f"{SERVE_HANDLES} handles of B_max 8192, horizon classes {pinmpc.horizon_classes_for(nf)}; "
+                              "window 2 s after 0.5 s warm-up")
         fsrv.close()
         del pool, fsrv
         torch.cuda.empty_cache()
@@ -568,7 +569,8 @@ def run_gpu(args):
                   "ms_per_solve": umt * 1e3,
                   "iters_mean": [float(r_["iters"].mean()) for r_ in res_],
                   "workload": "16384 envs: 8192 walking (8 point contacts) + 8192 Bernoulli-stance (2 foot wrenches), "
-                              "horizons U{5..40}, stage stride 40, both shapes solved concurrently (inputs resident)"}
+                              "horizons U{5..40}, stage stride 40, horizon classes (10, 20, 32, 40), both shapes solved concurrently "
+                              "(inputs resident)"}
 
     if rank != 0:
         return

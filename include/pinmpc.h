@@ -252,6 +252,23 @@ mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32
 mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx, int32_t rows, int32_t B,
                           void* stream);
 
+/* Horizon classes (optional; default one class).  The paper's method is
+ * parallel in the horizon: one warp per stage, an instance's round held by
+ * one CTA sized for the handle's stage stride N, so an instance with a short
+ * horizon occupies a CTA sized for N.  With classes, each ADMM round runs
+ * once per class: instances whose horizon is at most caps[0] on CTAs sized
+ * for caps[0] stages (several per SM when they fit), those up to caps[1] on
+ * the next size, ..., the rest on CTAs sized for N.  The instances still
+ * running after a round join their class's list.  Results are identical
+ * with and without classes (the same arithmetic per instance); only the
+ * placement differs.  Each solve adds one launch per class and round.
+ *   caps: n ascending stage counts in [1, N_max] (host memory, copied); caps
+ *         at or above a solve's N are ignored by that solve.  n: 0 .. 3
+ *         (0 = one class).  MPC_ERR_INVALID_ARG otherwise.  Drops the
+ *         captured graphs (mpc_set_graph_mode).
+ * This is an implementation choice with no counterpart in the paper. */
+mpc_status mpc_set_horizon_classes(mpc_handle* h, const int32_t* caps, int32_t n);
+
 /* CUDA-graph replay of the solve (no counterpart in the paper; a launch-cost
  * aid).  With enable != 0, mpc_solve_batch records its device work (flag
  * resets, the factor kernel and the whole round schedule) into a CUDA graph

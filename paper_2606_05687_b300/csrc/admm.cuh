@@ -524,18 +524,22 @@ __device__ void round_fail(const RoundArgs& a, int b, int status) {
 }
 
 // One round of ADMM iterations (a.m0, a.m1] for one instance per CTA; the
-// factor cache and the iterate stay in global memory between rounds.
-template <class D, int MAXT>
+// factor cache and the iterate stay in global memory between rounds.  The
+// CTA's shared memory holds cap stages: N, or with CAPPED a.cap < N (the
+// launch serves a horizon class whose horizons all fit).  The uncapped form
+// is compiled with cap = N throughout.
+template <class D, int MAXT, bool CAPPED>
 __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float* smem, int buf) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     constexpr bool TWO = RegT<D>::kTwo;
     if (a.done[b]) return;
-    const RoundSmem<D> L(a.N, a.dbl != 0);
+    const int cap = CAPPED ? a.cap : a.N;
+    const RoundSmem<D> L(cap, a.dbl != 0);
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const float* rec = a.rec + (size_t)b * a.irec;
     const float* tail = rec + (size_t)a.n_rec * D::SREC;
     const int Nh0 = __float_as_int(__ldg(tail + D::tH));
-    const int Nh = (Nh0 >= 1 && Nh0 <= a.N) ? Nh0 : 0;
+    const int Nh = (Nh0 >= 1 && Nh0 <= cap) ? Nh0 : 0;
     if (Nh == 0) {
         round_fail<D>(a, b, kBadHorizon);
         return;
@@ -550,7 +554,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     RCtx<D> c;
     c.var = smem + L.var; c.xb = smem + L.xb; c.tmp = smem + L.tmp; c.pre = smem + L.pre;
     c.fac = smem + (buf ? L.fac2 : L.fac); c.part = smem + L.part;
-    c.N = a.N; c.Nh = Nh; c.rho = a.rho;
+    c.N = cap; c.Nh = Nh; c.rho = a.rho;
     float* sd = smem + (buf ? L.sd2 : L.sd);
     if (!a.dbl) {  // otherwise the records are already there (TMA)
         const float4* src = reinterpret_cast<const float4*>(rec);
@@ -561,14 +565,15 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     for (int i = tid; i < NBP; i += nthr)
         c.xb[i] = i < NX ? __ldg(tail + D::tXI0 + i) : (i < NB ? __ldg(tail + D::tUP + i - NX) : 0.0f);
     // vectors read as float4 need finite padding
-    for (int e = NBP + tid; e < (a.N + 1) * NBP; e += nthr) c.xb[e] = 0.0f;
-    for (int e = tid; e < a.N * RoundSmem<D>::kTmp * NBP; e += nthr) c.tmp[e] = 0.0f;
+    for (int e = NBP + tid; e < (cap + 1) * NBP; e += nthr) c.xb[e] = 0.0f;
+    for (int e = tid; e < cap * RoundSmem<D>::kTmp * NBP; e += nthr) c.tmp[e] = 0.0f;
     __syncthreads();
     auto stage = [&](int k) { return sd + k * D::SREC; };
     auto mask = [&](int k) { return __float_as_uint(stage(k)[D::oMASK]); };
     float* gcache = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
     float* gstate = a.state + (size_t)b * RoundState<D>::floats(a.N);
-    const int nvar = RoundState<D>::var_floats(a.N);
+    const int nvar = RoundState<D>::var_floats(a.N);  // global layout: N stages per buffer
+    const int lvar = RoundState<D>::var_floats(cap);  // shared-memory layout: cap stages per buffer
     // per-stage constants: qbar, 1/D' = 1/(Q+rho | R+2rho), 1/D = 1/(Q+rho | R+rho)
     for (int e = tid; e < Nh * NBP; e += nthr) {
         const int k = e / NBP, i = e % NBP;
@@ -594,7 +599,14 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     }
     const bool warm = a.m0 == 0 && b < a.warm_B;  // start from the shifted previous iterate
     if (a.m0 == 0) {
-        if (!warm) for (int e = tid; e < nvar; e += nthr) c.var[e] = 0.0f;
+        if (!warm) {
+            for (int e = tid; e < lvar; e += nthr) c.var[e] = 0.0f;
+            // stages past cap start (and stay) zero, as when all N are held
+            for (int e = tid; cap < a.N && e < 2 * (a.N - cap) * 5 * NBP; e += nthr) {
+                const int bf = e / ((a.N - cap) * 5 * NBP), r = e % ((a.N - cap) * 5 * NBP);
+                gstate[RoundState<D>::at(a.N, bf, cap, 0) + r] = 0.0f;
+            }
+        }
         for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
         if (tid == 0) {
             a.out_npol[b] = 0;
@@ -602,9 +614,17 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         }
     }
     if (a.m0 > 0 || warm) {
-        const float4* src = reinterpret_cast<const float4*>(gstate);
-        float4* dst = reinterpret_cast<float4*>(c.var);
-        for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
+        if (cap == a.N) {
+            const float4* src = reinterpret_cast<const float4*>(gstate);
+            float4* dst = reinterpret_cast<float4*>(c.var);
+            for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
+        } else {
+            for (int bf = 0; bf < 2; ++bf) {
+                const float4* src = reinterpret_cast<const float4*>(gstate + RoundState<D>::at(a.N, bf, 0, 0));
+                float4* dst = reinterpret_cast<float4*>(c.var + RoundState<D>::at(cap, bf, 0, 0));
+                for (int e = tid; e < lvar / 8; e += nthr) dst[e] = src[e];
+            }
+        }
     }
     // stage matrix and per-stage constants into registers
     const int j = warp < Nh ? warp : 0;
@@ -688,10 +708,16 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         }
         cb = 1 - cb;
     }
-    {
+    if (cap == a.N) {
         const float4* src = reinterpret_cast<const float4*>(c.var);
         float4* dst = reinterpret_cast<float4*>(gstate);
         for (int e = tid; e < nvar / 4; e += nthr) dst[e] = src[e];
+    } else {
+        for (int bf = 0; bf < 2; ++bf) {
+            const float4* src = reinterpret_cast<const float4*>(c.var + RoundState<D>::at(cap, bf, 0, 0));
+            float4* dst = reinterpret_cast<float4*>(gstate + RoundState<D>::at(a.N, bf, 0, 0));
+            for (int e = tid; e < lvar / 8; e += nthr) dst[e] = src[e];
+        }
     }
     if (active && lane < D::NC && a.m1 > a.m0) a.modes[((size_t)b * a.N + j) * D::NC + lane] = R.mw;
     if (tid == 0) {
@@ -742,13 +768,14 @@ __global__ void warm_shift_kernel(float* state, const float* rec, int irec, int 
 
 // One round of ADMM iterations (a.m0, a.m1]: persistent CTAs (one per SM), each
 // taking instances of the round's list until it is exhausted.
-// Thread 0: start the TMA copies of instance b's records (the first a.N
+// Thread 0: start the TMA copies of instance b's records (the first cap
 // stages) and factors into buffer buf, completing on bar[buf].
-template <class D>
+template <class D, bool CAPPED>
 __device__ __noinline__ void round_fetch(const RoundArgs& a, float* smem, uint64_t* bar, int b, int buf) {
-    const RoundSmem<D> L(a.N, true);
-    const uint32_t rec_bytes = (uint32_t)(a.N * D::SREC * sizeof(float));
-    const uint32_t fac_bytes = (uint32_t)(RoundSmem<D>::cache_floats(a.N) * sizeof(float));
+    const int cap = CAPPED ? a.cap : a.N;
+    const RoundSmem<D> L(cap, true);
+    const uint32_t rec_bytes = (uint32_t)(cap * D::SREC * sizeof(float));
+    const uint32_t fac_bytes = (uint32_t)(RoundSmem<D>::cache_floats(cap) * sizeof(float));
     mbar_arrive_expect_tx(&bar[buf], rec_bytes + fac_bytes);
     bulk_copy_g2s(smem + (buf ? L.sd2 : L.sd), a.rec + (size_t)b * a.irec, rec_bytes, &bar[buf]);
     bulk_copy_g2s(smem + (buf ? L.fac2 : L.fac), a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N), fac_bytes,
@@ -758,7 +785,7 @@ __device__ __noinline__ void round_fetch(const RoundArgs& a, float* smem, uint64
 // With a.dbl, thread 0 starts the TMA copies of the next instance's records
 // and factors into the other buffer as soon as it knows that instance, so
 // they arrive while the current instance iterates.
-template <class D, int MAXT>
+template <class D, int MAXT, bool CAPPED = false>
 __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int item;
@@ -770,13 +797,13 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     }
     int b = next_instance(a, 0, &item);  // starts with a barrier: the initialisation is visible
     if (b < 0) return;
-    if (dbl && threadIdx.x == 0) round_fetch<D>(a, smem, bar, b, 0);
+    if (dbl && threadIdx.x == 0) round_fetch<D, CAPPED>(a, smem, bar, b, 0);
     for (int it = 0;; ++it) {
         // buffers alternate, so buffer it & 1 completes its (it >> 1)-th phase now
         const int cur = dbl ? (it & 1) : 0;
         const int bn = next_instance(a, 0, &item);
         if (dbl) {
-            if (bn >= 0 && threadIdx.x == 0) round_fetch<D>(a, smem, bar, bn, cur ^ 1);
+            if (bn >= 0 && threadIdx.x == 0) round_fetch<D, CAPPED>(a, smem, bar, bn, cur ^ 1);
             const bool ok = __syncthreads_and(mbar_wait(&bar[cur], (uint32_t)(it >> 1) & 1u));
             if (!ok) {
                 // the copies did not arrive: report this instance, let the other
@@ -786,7 +813,7 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
                 return;
             }
         }
-        round_instance<D, MAXT>(a, b, smem, cur);
+        round_instance<D, MAXT, CAPPED>(a, b, smem, cur);
         if (bn < 0) break;
         b = bn;
     }

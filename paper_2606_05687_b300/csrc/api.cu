@@ -47,6 +47,7 @@ struct Shape {
     void (*launch_state_copy)(const float* src, const int* sidx, int src_rows, float* dst, const int* didx, int dst_rows,
                               const float* rec, int irec, int n_rec, int B, int N, int shift, cudaStream_t s);
     cudaError_t (*set_state_copy_attr)(int bytes);
+    void (*launch_bin)(const RoundArgs&, int B, cudaStream_t);
 };
 
 template <class D>
@@ -71,6 +72,10 @@ cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(round2_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(round2_kernel<D, 640, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(round2_kernel<D, 1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(round_cl_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(round_cl_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
@@ -80,16 +85,26 @@ cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
 template <class D>
 void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
     // register-heavy form for up to 20 stages per CTA (640 threads), 64-register
-    // form above; B persistent workers: CTAs, or CTA pairs above 32 stages
-    if (a.N > 32) {
-        const int nl = (a.N + 1) / 2;
+    // form above; B persistent workers: CTAs, or CTA pairs above 32 stages.
+    // The launch's stage capacity is a.cap (its horizon class's, N for one class).
+    const int n = a.cap;
+    if (n > 32) {
+        const int nl = (n + 1) / 2;
         if (nl <= 20) round_cl_kernel<D, 640><<<2 * B, 32 * nl, smem, s>>>(a);
         else round_cl_kernel<D, 1024><<<2 * B, 32 * nl, smem, s>>>(a);
-    } else if (a.N <= 20) {
-        round2_kernel<D, 640><<<B, 32 * a.N, smem, s>>>(a);
+    } else if (n < a.N) {
+        // a horizon class below N: CTAs sized for n stages
+        if (n <= 20) round2_kernel<D, 640, true><<<B, 32 * n, smem, s>>>(a);
+        else round2_kernel<D, 1024, true><<<B, 32 * n, smem, s>>>(a);
+    } else if (n <= 20) {
+        round2_kernel<D, 640><<<B, 32 * n, smem, s>>>(a);
     } else {
-        round2_kernel<D, 1024><<<B, 32 * a.N, smem, s>>>(a);
+        round2_kernel<D, 1024><<<B, 32 * n, smem, s>>>(a);
     }
+}
+template <class D>
+void launch_bin_t(const RoundArgs& a, int B, cudaStream_t s) {
+    bin_classes_kernel<D><<<(B + 255) / 256, 256, 0, s>>>(a);
 }
 template <class D>
 void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
@@ -137,7 +152,7 @@ Shape make_shape() {
     return Shape{D::SREC,         D::TAIL,           launch_pack_t<D>,     polish_smem_t<D>,     state_floats_t<D>,
                  set_round_attrs_t<D>, launch_round_t<D>, launch_polish_t<D>, round_smem_t<D>,
                  cache_floats_t<D>, launch_factor_t<D>, resident_per_sm_t<D>, launch_warm_shift_t<D>,
-                 set_warm_attr_t<D>, launch_state_copy_t<D>, set_state_copy_attr_t<D>};
+                 set_warm_attr_t<D>, launch_state_copy_t<D>, set_state_copy_attr_t<D>, launch_bin_t<D>};
 }
 
 bool pick_shape(int nx, int nc, int cd, Shape* out) {
@@ -181,8 +196,10 @@ struct mpc_handle {
     uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
     int* done = nullptr;         // [B_max]
     int* flags = nullptr;        // [B_max] input-check bits of the factor kernel
-    int* lists = nullptr;        // [2][B_max] instances still running, by round parity
-    int* work = nullptr;         // [4] round cursor, polish cursor, list counts [2]
+    int* lists = nullptr;        // [2][kMaxClasses][B_max] instances still running, by round parity and horizon class
+    int* work = nullptr;         // [kMaxClasses] round cursors, then list counts [2][kMaxClasses]
+    int ncls_req = 0;            // horizon classes below N (mpc_set_horizon_classes), ascending caps
+    int cls_req[kMaxClasses] = {};
     int sms = 0;                 // streaming multiprocessors of the device
     int optin_smem = 0;          // opt-in shared memory per CTA
     int round_attr = 0;          // dynamic shared memory the round kernel is set up for
@@ -451,7 +468,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
     const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
-    const size_t round_b = cache_b + state_b + 2 * modes_b + 2 * B * sizeof(int) + sizeof(int) + kst_b;
+    const size_t round_b = cache_b + state_b + 2 * modes_b + (2 + 2 * kMaxClasses) * B * sizeof(int) + sizeof(int) + kst_b;
     h->bytes = rec_b + xi_b + u_b + small_b + round_b;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }
@@ -473,8 +490,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->modes, modes_b) == cudaSuccess && cudaMalloc(&h->lastm, modes_b) == cudaSuccess &&
               cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->flags, B * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&h->lists, 2 * B * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&h->work, 4 * sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess;
+              cudaMalloc(&h->lists, 2 * kMaxClasses * B * sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&h->work, 3 * kMaxClasses * sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         const unsigned long long want = h->bytes;
@@ -576,9 +593,49 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     return MPC_OK;
 }
 
+// Launch form of each horizon class's round kernel: stage capacity, TMA
+// double buffering, dynamic shared memory, persistent workers.
+struct SolvePlan {
+    int ncls;
+    struct { int cap, dbl, smem, grid; } cls[kMaxClasses];
+};
+
+// The classes of a solve: the requested caps below N, then N itself; each
+// class's CTAs hold cap stages (CTA pairs above 32).  Raises the round
+// kernels' shared-memory attribute when a class needs more than it allows.
+static mpc_status plan_solve(mpc_handle* h, int B, SolvePlan* p) {
+    const int N = h->N_set;
+    p->ncls = 0;
+    for (int i = 0; i < h->ncls_req; ++i)
+        if (h->cls_req[i] < N) p->cls[p->ncls++].cap = h->cls_req[i];
+    p->cls[p->ncls++].cap = N;
+    int need = 0;
+    for (int k = 0; k < p->ncls; ++k) {
+        auto& q = p->cls[k];
+        if (q.cap > 32) {
+            q.dbl = 0;
+            q.smem = h->shape.round_smem(q.cap, false);
+            q.grid = h->sms * h->shape.resident_per_sm(0, q.cap, q.smem) / 2;
+        } else {
+            const int sd = h->shape.round_smem(q.cap, true);
+            q.dbl = sd <= h->optin_smem;
+            q.smem = q.dbl ? sd : h->shape.round_smem(q.cap, false);
+            q.grid = h->sms * h->shape.resident_per_sm(0, q.cap, q.smem);
+        }
+        q.grid = std::max(1, std::min(B, q.grid));
+        need = std::max(need, q.smem);
+    }
+    if (need > h->round_attr) {
+        cudaError_t e = h->shape.set_round_attrs(need, h->shape.polish_smem(h->cfg.N_max));
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFuncSetAttribute");
+        h->round_attr = need;
+    }
+    return MPC_OK;
+}
+
 // The solve's device work for instances [0, B) on stream st: flag resets,
 // the factor kernel and the whole round schedule (no host synchronisation).
-static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStream_t st, int round_smem) {
+static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStream_t st, const SolvePlan& plan) {
     const mpc_config& c = h->cfg;
     cudaError_t e;
     const int polish_smem = h->shape.polish_smem(h->N_set);
@@ -602,11 +659,22 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
     // persistent CTAs work through the round's list of running instances and
     // the polish kernel's CTAs index it, so a round with few or no instances
     // left costs one short launch of each kernel
-    int* cursor = h->work;
-    int* cnt = h->work + 2;
-    // persistent workers: CTAs, or CTA pairs (two SMs each) above 32 stages
-    const int round_grid = std::max(
-        1, std::min(B, h->sms * h->shape.resident_per_sm(0, h->N_set, round_smem) / (h->N_set > 32 ? 2 : 1)));
+    int* cursor = h->work;             // [kMaxClasses]
+    int* cnt = h->work + kMaxClasses;  // [2][kMaxClasses]
+    const int K = plan.ncls;
+    const size_t LS = (size_t)kMaxClasses * c.B_max;  // one parity's lists
+    r.ncls = K;
+    r.cls_stride = c.B_max;
+    for (int k = 0; k < K; ++k) r.cls_cap[k] = plan.cls[k].cap;
+    if (K > 1) {
+        // round 0's lists: every instance in its horizon class's list
+        RoundArgs rb = r;
+        rb.list_out = h->lists;
+        rb.cnt_out = cnt;
+        if ((e = cudaMemsetAsync(cnt, 0, K * sizeof(int), st)) != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync");
+        if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_bin(rb, B, st); })) != cudaSuccess)
+            return cuda_fail(h, e, "class binning launch");
+    }
     const int polish_grid = B;
     int m0 = 0, round = 0;
     double interval = c.check_every;
@@ -621,20 +689,33 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
         const int in = round & 1, out = in ^ 1;
         r.m0 = m0;
         r.m1 = m1;
-        r.list_in = round == 0 ? nullptr : h->lists + (size_t)in * c.B_max;
-        r.cnt_in = cnt + in;
-        r.list_out = h->lists + (size_t)out * c.B_max;
-        r.cnt_out = cnt + out;
+        // round 0 of a single class takes every instance without a list
+        r.list_in = (round == 0 && K == 1) ? nullptr : h->lists + in * LS;
+        r.cnt_in = cnt + in * kMaxClasses;
+        r.list_out = h->lists + out * LS;
+        r.cnt_out = cnt + out * kMaxClasses;
         r.cursor = cursor;
         r.warm_B = (h->warm_N == h->N_set) ? std::min(h->warm_B, B) : 0;
         // the few instances left after two rounds get more refinement: the
         // allowance doubles per round from round 2 on (up to 32)
         r.refine_steps = std::min(32, c.refine_steps << std::min(std::max(round - 1, 0), 4));
-        if ((e = cudaMemsetAsync(cursor, 0, 2 * sizeof(int), st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(cnt + out, 0, sizeof(int), st)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(cursor, 0, K * sizeof(int), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(r.cnt_out, 0, K * sizeof(int), st)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemsetAsync");
-        if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_round(r, round_grid, round_smem, st); })) != cudaSuccess)
-            return cuda_fail(h, e, "round kernel launch");
+        // one round kernel launch per horizon class, each on its class's list
+        for (int k = 0; k < K; ++k) {
+            RoundArgs rk = r;
+            rk.cap = plan.cls[k].cap;
+            rk.dbl = plan.cls[k].dbl;
+            rk.cursor = cursor + k;
+            if (r.list_in) {
+                rk.list_in = r.list_in + (size_t)k * c.B_max;
+                rk.cnt_in = r.cnt_in + k;
+            }
+            const int grid = plan.cls[k].grid, smem = plan.cls[k].smem;
+            if ((e = timed_launch(h, kClassRound, st, [&] { h->shape.launch_round(rk, grid, smem, st); })) != cudaSuccess)
+                return cuda_fail(h, e, "round kernel launch");
+        }
         if ((e = timed_launch(h, kClassPolish, st, [&] { h->shape.launch_polish(r, polish_grid, polish_smem, st); })) != cudaSuccess)
             return cuda_fail(h, e, "polish kernel launch");
         if (round < (int)h->round_events.size() && h->round_events[round] &&
@@ -664,16 +745,13 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
-    // double-buffered records and factors (TMA prefetch) when they fit
-    const int smem_single = h->shape.round_smem(h->N_set, false), smem_dbl = h->shape.round_smem(h->N_set, true);
-    const bool dbl = h->N_set <= 32 && smem_dbl <= h->optin_smem;
-    const int round_smem = dbl ? smem_dbl : smem_single;
-    if (round_smem > h->round_attr) {
-        if ((e = h->shape.set_round_attrs(round_smem, h->shape.polish_smem(c.N_max))) != cudaSuccess)
-            return cuda_fail(h, e, "cudaFuncSetAttribute");
-        h->round_attr = round_smem;
-    }
-    r.dbl = dbl ? 1 : 0;
+    // each horizon class's launch form (double-buffered records and factors,
+    // TMA prefetch, where they fit)
+    SolvePlan plan;
+    mpc_status ps = plan_solve(h, B, &plan);
+    if (ps != MPC_OK) return ps;
+    r.dbl = plan.cls[plan.ncls - 1].dbl;
+    r.cap = h->N_set;
     r.warm_B = (h->warm_N == h->N_set) ? std::min(h->warm_B, B) : 0;
     mpc_status ms = MPC_OK;
     if (h->graph_mode && !h->timing) {
@@ -688,7 +766,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
                 return cuda_fail(h, e, "cudaStreamCreateWithFlags");
             if ((e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
                 return cuda_fail(h, e, "cudaStreamBeginCapture");
-            ms = enqueue_solve(h, B, r, h->capture_stream, round_smem);
+            ms = enqueue_solve(h, B, r, h->capture_stream, plan);
             cudaGraph_t g = nullptr;
             const cudaError_t ee = cudaStreamEndCapture(h->capture_stream, &g);
             if (ms != MPC_OK) {
@@ -711,7 +789,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         if ((e = cudaGraphLaunch(it->exec, st)) != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
         ++h->graph_replays;
     } else {
-        ms = enqueue_solve(h, B, r, st, round_smem);
+        ms = enqueue_solve(h, B, r, st, plan);
         if (ms != MPC_OK) return ms;
     }
     h->have_solution = true;
@@ -843,6 +921,19 @@ mpc_status mpc_set_round_events(mpc_handle* h, void* const* events, int32_t n) {
     for (int i = 0; i < n; ++i) h->round_events[i] = static_cast<cudaEvent_t>(events[i]);
     cudaSetDevice(h->cfg.device);
     drop_graphs(h);  // captured solves hold the previous events
+    return MPC_OK;
+}
+
+mpc_status mpc_set_horizon_classes(mpc_handle* h, const int32_t* caps, int32_t n) {
+    if (!h) return MPC_ERR_INVALID_ARG;
+    if (n < 0 || n > kMaxClasses - 1 || (n > 0 && !caps))
+        return fail(h, MPC_ERR_INVALID_ARG, "n=%d horizon classes (0..%d, caps required)", n, kMaxClasses - 1);
+    for (int i = 0; i < n; ++i)
+        if (caps[i] < 1 || caps[i] > h->cfg.N_max || (i > 0 && caps[i] <= caps[i - 1]))
+            return fail(h, MPC_ERR_INVALID_ARG, "class caps must ascend within [1, N_max=%d]", h->cfg.N_max);
+    h->ncls_req = n;
+    for (int i = 0; i < n; ++i) h->cls_req[i] = caps[i];
+    drop_graphs(h);  // captured solves hold the previous launch sequence
     return MPC_OK;
 }
 

@@ -18,6 +18,9 @@ struct RoundState {
     static constexpr int sAlpha = 0, sCprev = 1, sWgt = 2, sRestart = 3, sCb = 4;
 };
 
+// Horizon classes of one solve (mpc_set_horizon_classes): at most this many.
+constexpr int kMaxClasses = 4;
+
 struct RoundArgs {
     const float* rec;
     int irec, n_rec, N;
@@ -51,7 +54,37 @@ struct RoundArgs {
     unsigned long long* out_bits;
     int* out_npol;
     int* out_piv;            // [B] free pivots eliminated by the polish
+    // horizon classes: the work lists hold one list per class (class c at
+    // offset c * cls_stride of list_in / list_out, its count at cnt_in[c] /
+    // cnt_out[c]); the polish kernel reads all ncls lists of list_in and
+    // appends each running instance to its class's list of list_out.  A round
+    // kernel launch serves one class: its list and count, and CTAs sized for
+    // cap stages (every horizon of the class fits; N for a single class)
+    int ncls, cls_stride, cap;
+    int cls_cap[kMaxClasses];
 };
+
+// Class of an instance with horizon Nh: the first class whose cap holds it;
+// a horizon outside [1, N] goes to the last class (cap N), whose round kernel
+// reports it.
+__host__ __device__ inline int horizon_class(int Nh, int N, int ncls, const int* caps) {
+    if (Nh >= 1 && Nh <= N)
+        for (int c = 0; c + 1 < ncls; ++c)
+            if (Nh <= caps[c]) return c;
+    return ncls - 1;
+}
+
+// Round 0 with several classes: instance b of the batch goes to its class's
+// list (list_out / cnt_out of `a`, counts zeroed before).  Order within a
+// list is arbitrary: every instance is solved on its own.
+template <class D>
+__global__ void bin_classes_kernel(RoundArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.B) return;
+    const float* tail = a.rec + (size_t)b * a.irec + (size_t)a.n_rec * D::SREC;
+    const int cl = horizon_class(__float_as_int(tail[D::tH]), a.N, a.ncls, a.cls_cap);
+    a.list_out[(size_t)cl * a.cls_stride + atomicAdd(a.cnt_out + cl, 1)] = b;
+}
 
 // Next instance for a persistent CTA (all threads get the same value), or -1
 // when the round's list is exhausted; `which` selects the kernel's cursor.

@@ -818,17 +818,32 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
     }
     if (c.tid == 0) {
         a.out_npol[b] = npol;
-        a.list_out[atomicAdd(a.cnt_out, 1)] = b;  // still running: next round
+        // still running: next round, in its horizon class's list
+        const int cl = horizon_class(c.Nh, a.N, a.ncls, a.cls_cap);
+        a.list_out[(size_t)cl * a.cls_stride + atomicAdd(a.cnt_out + cl, 1)] = b;
     }
 }
 
 // Polish / certify / refine after a round: CTA i takes slot i of the round's
-// list (grid = batch size; slots past the list's length return at once).
+// lists, the classes' lists taken one after another (grid = batch size;
+// slots past their total length return at once).
 template <class D>
 __global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float psm[];
-    const int i = blockIdx.x;
-    const int b = a.list_in ? (i < *a.cnt_in ? a.list_in[i] : -1) : (i < a.B ? i : -1);
+    int b = -1;
+    if (!a.list_in) {
+        b = blockIdx.x < a.B ? (int)blockIdx.x : -1;
+    } else {
+        int i = blockIdx.x;
+        for (int cl = 0; cl < a.ncls; ++cl) {
+            const int n = a.cnt_in[cl];
+            if (i < n) {
+                b = a.list_in[(size_t)cl * a.cls_stride + i];
+                break;
+            }
+            i -= n;
+        }
+    }
     if (b < 0) return;
     polish_instance<D>(a, b, psm);
 }

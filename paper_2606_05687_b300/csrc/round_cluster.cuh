@@ -47,7 +47,7 @@ __device__ __forceinline__ T* cluster_peer(T* p, uint32_t rank) {
 constexpr int kClusterMaxN = 64;
 
 // One round (a.m0, a.m1] of one instance by CTA `rank` of the pair; NL is the
-// local stage capacity ceil(a.N / 2).  The instance's horizon Nh (1..a.N)
+// local stage capacity ceil(cap / 2).  The instance's horizon Nh (1..cap)
 // was checked by the caller.
 template <class D, int MAXT>
 __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, float* smem, uint32_t rank, int NL) {
@@ -110,7 +110,14 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
     const bool warm = a.m0 == 0 && b < a.warm_B;
     const int lvar = 5 * NBP * nloc;  // floats of this CTA's stages in one buffer
     if (a.m0 == 0) {
-        if (!warm) for (int e = tid; e < RoundState<D>::var_floats(NL); e += nthr) c.var[e] = 0.0f;
+        if (!warm) {
+            for (int e = tid; e < RoundState<D>::var_floats(NL); e += nthr) c.var[e] = 0.0f;
+            // stages past the horizon start (and stay) zero, as in the one-CTA form
+            for (int e = tid; rank == 0 && e < 2 * (a.N - Nh) * 5 * NBP; e += nthr) {
+                const int bf = e / ((a.N - Nh) * 5 * NBP), r = e % ((a.N - Nh) * 5 * NBP);
+                gstate[RoundState<D>::at(a.N, bf, Nh, 0) + r] = 0.0f;
+            }
+        }
         if (rank == 0) {
             for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
             if (tid == 0) {
@@ -235,14 +242,16 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
     }
 }
 
-// Persistent pairs: grid = 2 x pairs, block = 32 ceil(a.N / 2) threads
-// (MAXT at least that), dynamic shared memory RoundSmem<D>(ceil(a.N / 2)).
+// Persistent pairs: grid = 2 x pairs, block = 32 ceil(cap / 2) threads
+// (MAXT at least that), dynamic shared memory RoundSmem<D>(ceil(cap / 2)),
+// cap = a.cap: the longest horizon the launch takes.
 template <class D, int MAXT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(MAXT, 1) round_cl_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int item[2];  // instance (or -1: no work left) and the action for it
     const uint32_t rank = cluster_rank();
-    const int NL = (a.N + 1) / 2;
+    const int cap = a.cap;
+    const int NL = (cap + 1) / 2;
     int* peer_item = cluster_peer(item, rank ^ 1u);
     for (;;) {
         // both CTAs are done with the previous instance, including each
@@ -259,7 +268,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(MAXT, 1) round_cl_ke
                 const int Nh = __float_as_int(tail[D::tH]);
                 if (a.done[b]) {
                     act = 1;
-                } else if (Nh < 1 || Nh > a.N) {
+                } else if (Nh < 1 || Nh > cap) {
                     act = 2 + kBadHorizon;
                 } else if (a.m0 == 0 && a.flags[b]) {
                     act = 2 + ((a.flags[b] & 1) ? kNonFinite : kBadSet);

@@ -17,13 +17,18 @@ from . import pinmpc
 
 class MixedSolver:
     """One handle and one stream per sub-batch shape; `solve` enqueues every
-    sub-batch and waits for all of them."""
+    sub-batch and waits for all of them.  With `classes` each handle runs its
+    ADMM rounds per horizon class (mpc_set_horizon_classes)."""
 
-    def __init__(self, batches: List, **overrides):
+    def __init__(self, batches: List, classes: bool = True, **overrides):
         import torch
 
         self.torch = torch
         self.solvers = [pinmpc.solver_for(b, **overrides) for b in batches]
+        if classes:
+            # ragged horizons: each round on CTAs sized for each horizon class
+            for s, b in zip(self.solvers, batches):
+                s.set_horizon_classes(pinmpc.horizon_classes_for(b.N))
         self.streams = [torch.cuda.Stream() for _ in batches]
         self.shapes = [(b.nx, b.nc, b.contact_dim, b.B, b.N) for b in batches]
 

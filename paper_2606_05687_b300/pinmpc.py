@@ -84,6 +84,8 @@ def load() -> ctypes.CDLL:
     lib.mpc_load_state.restype = ctypes.c_int
     lib.mpc_set_round_events.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_round_events.restype = ctypes.c_int
+    lib.mpc_set_horizon_classes.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+    lib.mpc_set_horizon_classes.restype = ctypes.c_int
     lib.mpc_set_graph_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_graph_mode.restype = ctypes.c_int
     lib.mpc_get_graph_stats.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -228,6 +230,12 @@ class Solver:
         self._check(self.lib.mpc_get_graph_stats(self.h, ctypes.byref(c), ctypes.byref(r)), "mpc_get_graph_stats")
         return c.value, r.value
 
+    def set_horizon_classes(self, caps):
+        """Round-kernel horizon classes (ascending stage counts; [] = one class)."""
+        arr = (ctypes.c_int32 * max(len(caps), 1))(*[int(c) for c in caps])
+        self._check(self.lib.mpc_set_horizon_classes(self.h, arr if caps else None, len(caps)),
+                    "mpc_set_horizon_classes")
+
     def set_kernel_timing(self, enable: bool):
         self._check(self.lib.mpc_set_kernel_timing(self.h, 1 if enable else 0), "mpc_set_kernel_timing")
 
@@ -281,6 +289,16 @@ def device_inputs(batch, device="cuda", pin_host=False):
     for k, t in out.items():
         out[k] = t.pin_memory() if pin_host else t.to(device)
     return out
+
+
+# Horizon classes for ragged batches: 10 stages (two CTAs per SM), 20 (the
+# 640-thread form with TMA prefetch), 32 (one CTA), then the stride itself.
+RAGGED_CLASSES = (10, 20, 32)
+
+
+def horizon_classes_for(N: int) -> list:
+    """The RAGGED_CLASSES below a stage stride N."""
+    return [c for c in RAGGED_CLASSES if c < N]
 
 
 def round_schedule(cfg: MpcConfig) -> list:

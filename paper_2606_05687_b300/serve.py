@@ -42,6 +42,8 @@ STAGE_KEYS = ("A", "Bm", "e", "Q", "R", "ry", "ru", "mu", "fmax", "mask", "xi0",
 class BatchServer:
     """Continuous batching over ``n_handles`` solver handles.
 
+    ``horizon_classes`` (ascending stage counts) makes each handle run its
+    ADMM rounds per horizon class, for pools with ragged horizons.
     ``pool`` holds the stage data of every environment the requests refer to
     (torch tensors on the device, keyed like ``pinmpc.device_inputs``; row e
     is environment e).  ``clock`` returns seconds.  Request r (in submission
@@ -51,7 +53,7 @@ class BatchServer:
 
     def __init__(self, pool: Dict[str, "object"], nx: int, nc: int, contact_dim: int, B_max: int, N: int,
                  n_handles: int = 2, clock: Callable[[], float] = time.perf_counter,
-                 warm_shift: Optional[int] = None, early: bool = True, **overrides):
+                 warm_shift: Optional[int] = None, early: bool = True, horizon_classes=None, **overrides):
         import torch
         self.torch = torch
         self.pool = pool
@@ -62,6 +64,8 @@ class BatchServer:
         for _ in range(n_handles):
             cfg = pinmpc.default_config(nx, nc, contact_dim, B_max, N, **overrides)
             solver = pinmpc.Solver(cfg)
+            if horizon_classes:
+                solver.set_horizon_classes(list(horizon_classes))
             inputs = {k: torch.empty((B_max,) + tuple(pool[k].shape[1:]), dtype=pool[k].dtype, device=self.device)
                       for k in STAGE_KEYS}
             outs = dict(u=torch.empty((B_max, N, nc * contact_dim), dtype=torch.float32, device=self.device),
