@@ -50,9 +50,9 @@ KERNEL_HEADERS = {
 }
 MEASURED_TRAFFIC = {
     # profiles/polish_cta_kernel_walking_B4096_N20.md: round-0 launch (all 4096 instances)
-    "polish:7d93c83d42f52651": 293722624,
+    "polish:4000f8cef5a403b9": 290644736,
     # profiles/round2_kernel_walking_B4096_N20.md: round-0 launch
-    "round:f7bc678b37cd6105": 440435968,
+    "round:cd66cca8787595f5": 439440128,
 }
 
 
