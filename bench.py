@@ -543,6 +543,13 @@ def run_gpu(args):
         del pool, fsrv
         torch.cuda.empty_cache()
 
+    # measured FP32 FMA throughput (mpc_measure_fma_peak), median of three,
+    # with the clocks seen meanwhile: the measured denominator beside the
+    # derived peak
+    with Clocks(local) as clk_p:
+        fma_runs = [pinmpc.measure_fma_peak(local) for _ in range(3)]
+    fma_peak = statistics.median(fma_runs)
+
     uneven = None
     if not args.device_only:
         # uneven batching: 16384 environments, half point contacts (walking),
@@ -610,7 +617,11 @@ def run_gpu(args):
                      "traffic_note": "dram bytes read + written by the round-0 launch (all instances), one ncu capture",
                      "kernel": dom, "ms_per_launch": kernels[dom]["ms_per_launch"],
                      "timing": "per-launch CUDA events over the single_stream timed steps (no overlapping launches)",
-                     "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived; no FP32 peak is measured)",
+                     "peak_note": "148 SM x 128 FP32 lanes x 2 x 2032 MHz (derived)",
+                     "peak_measured": fma_peak, "frac_of_measured": achieved / fma_peak,
+                     "peak_measured_note": "FP32 FMA microbenchmark (mpc_measure_fma_peak: 8 chains per thread, "
+                                           "8 x 256 threads per SM), median of 3",
+                     "peak_measured_clocks": clk_p.summary(),
                      "kernels": kernels, "solve_ms": solve_avg, "pack_ms": statistics.mean(pack_ms), "src": h},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

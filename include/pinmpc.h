@@ -252,6 +252,16 @@ mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32
 mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx, int32_t rows, int32_t B,
                           void* stream);
 
+/* FP32 FMA throughput of `device` in TFLOP/s (FMA = 2 flops) into *tflops:
+ * a kernel of 8 independent FMA chains per thread, 8 CTAs of 256 threads per
+ * SM, `iters` steps per chain, timed with CUDA events after one warm-up
+ * launch.  The measured denominator beside the derived SMs x 128 lanes x 2
+ * x clock peak of a roofline; a measurement utility with no counterpart in
+ * the paper.  Allocates and frees a small output buffer.
+ * MPC_ERR_INVALID_ARG (null tflops, iters < 1, bad device), MPC_ERR_OOM,
+ * MPC_ERR_CUDA. */
+mpc_status mpc_measure_fma_peak(int32_t device, int32_t iters, double* tflops);
+
 /* Horizon classes (optional; default one class).  The paper's method is
  * parallel in the horizon: one warp per stage, an instance's round held by
  * one CTA sized for the handle's stage stride N, so an instance with a short

@@ -84,6 +84,8 @@ def load() -> ctypes.CDLL:
     lib.mpc_load_state.restype = ctypes.c_int
     lib.mpc_set_round_events.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_round_events.restype = ctypes.c_int
+    lib.mpc_measure_fma_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    lib.mpc_measure_fma_peak.restype = ctypes.c_int
     lib.mpc_set_horizon_classes.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
     lib.mpc_set_horizon_classes.restype = ctypes.c_int
     lib.mpc_set_graph_mode.argtypes = [ctypes.c_void_p, ctypes.c_int32]
@@ -289,6 +291,16 @@ def device_inputs(batch, device="cuda", pin_host=False):
     for k, t in out.items():
         out[k] = t.pin_memory() if pin_host else t.to(device)
     return out
+
+
+def measure_fma_peak(device: int = 0, iters: int = 4096) -> float:
+    """Measured FP32 FMA throughput of the device, TFLOP/s."""
+    lib = load()
+    out = ctypes.c_double()
+    st = lib.mpc_measure_fma_peak(device, iters, ctypes.byref(out))
+    if st != MPC_OK:
+        raise MpcError(st, "mpc_measure_fma_peak")
+    return out.value
 
 
 # Horizon classes for ragged batches: 10 stages (two CTAs per SM), 20 (the

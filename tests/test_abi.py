@@ -88,6 +88,7 @@ def test_argument_errors_without_device(P):
     assert lib.mpc_state_floats(None, 20) == 0
     assert lib.mpc_set_round_events(None, None, 0) == P.MPC_ERR_INVALID_ARG
     assert lib.mpc_set_horizon_classes(None, None, 0) == P.MPC_ERR_INVALID_ARG
+    assert lib.mpc_measure_fma_peak(0, 16, None) == P.MPC_ERR_INVALID_ARG
     assert lib.mpc_save_state(None, None, None, 1, 1, 1, None) == P.MPC_ERR_INVALID_ARG
     assert lib.mpc_load_state(None, None, None, 1, 1, None) == P.MPC_ERR_INVALID_ARG
     assert lib.mpc_get_graph_stats(None, None, None) == P.MPC_ERR_INVALID_ARG

@@ -50,3 +50,14 @@ def test_pivot_counts(pinmpc):
     # every Riccati scan eliminates between 0 and nu free pivots per stage
     assert np.all(piv >= 0) and np.all(piv <= pol * batch.N * batch.nu)
     assert np.all((pol == 0) == (piv == 0))
+
+
+def test_measured_fma_peak_is_near_the_derived_one(pinmpc):
+    """The FMA microbenchmark lands near SMs x 128 lanes x 2 x max clock."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    t = pinmpc.measure_fma_peak(0, iters=2048)
+    derived = props.multi_processor_count * 128 * 2 * 2.032e9 / 1e12
+    assert 0.5 * derived < t < 1.1 * derived, (t, derived)
+    with pytest.raises(pinmpc.MpcError):
+        pinmpc.measure_fma_peak(0, iters=0)
