@@ -39,6 +39,18 @@ SERVE_HANDLES = 4  # handles of the served-latency leg (requests answered as the
 KKT_TOL = 1e-5
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+
+
+def _measured_hbm_gbs() -> float:
+    """The measured copy bandwidth of the B300s, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6400.0
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 # dram bytes (read + write) per launch of a kernel class from one ncu capture,
 # keyed "class:hash of the headers that kernel is built from" (host code in the
 # .cu files does not enter); a changed kernel makes its entry stale (null)
@@ -595,6 +607,22 @@ def run_gpu(args):
     achieved = kernels[dom]["achieved_tflops"]
     solve_avg = statistics.mean(solve_ms)
     h = kernel_source_hash(dom)
+    # HBM: the pack kernel streams the caller's arrays in and the packed
+    # records out; a whole step moves at least the inputs and the outputs
+    nx_, nu_, nc_ = batch.nx, batch.nu, batch.nc
+    srec = (nx_ * nx_ + nx_ * nu_ + 3 * nx_ + 2 * nu_ + 2 * nc_ + 1 + 3) // 4 * 4
+    tail = (nx_ + nu_ + 1 + 3) // 4 * 4
+    in_bytes = sum(v.numel() * v.element_size() for v in t.values())
+    rec_bytes = B * (N * srec + tail) * 4
+    pack_gbs = (in_bytes + rec_bytes) / (kernels["pack"]["ms_per_launch"] * 1e-3) / 1e9 if "pack" in kernels else None
+    out_bytes = B * N * (nx_ + nu_) * 4 + B * (3 * 4 + 4) + B * N * 8
+    step_gbs = (in_bytes + out_bytes) / (ms_per_step * 1e-3) / 1e9
+    hbm = {"peak_gbs": HBM_PEAK_GBS, "pack_bytes_per_launch": in_bytes + rec_bytes, "pack_achieved_gbs": pack_gbs,
+           "pack_frac": pack_gbs / HBM_PEAK_GBS if pack_gbs else None,
+           "step_algorithmic_bytes": in_bytes + out_bytes, "step_achieved_gbs": step_gbs,
+           "step_frac": step_gbs / HBM_PEAK_GBS,
+           "note": "pack: caller arrays read + packed records written per launch; step: inputs read + outputs "
+                   "written once per solve (ms_per_step); peak: MEASURED_PEAKS.json hbm_gbs (copy)"}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -621,7 +649,7 @@ def run_gpu(args):
                      "peak_measured": fma_peak, "frac_of_measured": achieved / fma_peak,
                      "peak_measured_note": "FP32 FMA microbenchmark (mpc_measure_fma_peak: 8 chains per thread, "
                                            "8 x 256 threads per SM), median of 3",
-                     "peak_measured_clocks": clk_p.summary(),
+                     "peak_measured_clocks": clk_p.summary(), "hbm": hbm,
                      "kernels": kernels, "solve_ms": solve_avg, "pack_ms": statistics.mean(pack_ms), "src": h},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
