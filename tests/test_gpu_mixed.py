@@ -1,6 +1,6 @@
 """Uneven batching (mixed contact models, ragged horizons U{5..N}): the
-concurrent per-shape solve equals separate solves bit for bit, and sampled
-instances of both shapes match the oracle."""
+concurrent per-shape solve equals separate solves with the same handle
+settings bit for bit, and sampled instances of both shapes match the oracle."""
 import numpy as np
 import pytest
 
@@ -27,7 +27,11 @@ def test_mixed_shapes_and_ragged_horizons():
     got = ms.results()
     ms.close()
     for b, g in zip(batches, got):
-        ref = pinmpc.solve_workload(b)
+        # the same handle settings (horizon classes) solving the sub-batch alone
+        rs = pinmpc.solver_for(b)
+        rs.set_horizon_classes(pinmpc.horizon_classes_for(b.N))
+        ref = pinmpc.solve_workload(b, solver=rs)
+        rs.close()
         assert np.array_equal(g["u"], ref["u"]) and np.array_equal(g["status"], ref["status"])
         assert np.all(g["status"] == 0)
         short = [int(i) for i in np.argsort(b.horizon)[:2]] + [int(np.argmax(b.horizon)), 77]
