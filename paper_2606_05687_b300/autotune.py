@@ -1,8 +1,10 @@
 """Schedule autotuner: pick solve parameters for a workload by measurement.
 
 The paper fixes none of the schedule (check points, refinement steps and
-step, the penalty rho); the library's defaults were measured per shape on
-the walking and small centroidal workloads.  For
+step, the penalty rho) and none of the launch shapes; the library's
+defaults were measured per shape on the walking and small centroidal
+workloads.  Besides the schedule, a grid may hold "horizon_classes": the
+round kernel's CTA shapes for batches with ragged horizons.  For
 another workload (another model, horizon or contact set) `autotune` times
 trial solves of a representative batch on the device for each candidate
 configuration and returns the fastest of those that certify the most
@@ -71,11 +73,17 @@ def select_best(table: List[dict]) -> Optional[dict]:
 
 def time_config(batch, trials: int = 3, **overrides) -> dict:
     """Median device time (ms) of `trials` solves of `batch` with `overrides`,
-    after one warm-up solve, and how many instances were certified."""
+    after one warm-up solve, and how many instances were certified.  The
+    key "horizon_classes" (a tuple of stage counts) sets the handle's
+    round-kernel CTA shapes (mpc_set_horizon_classes); the others are
+    solver configuration fields."""
     import torch
 
-    s = pinmpc.solver_for(batch, **overrides)
+    cfg = {k: v for k, v in overrides.items() if k != "horizon_classes"}
+    s = pinmpc.solver_for(batch, **cfg)
     try:
+        if "horizon_classes" in overrides:
+            s.set_horizon_classes(list(overrides["horizon_classes"]))
         t = pinmpc.device_inputs(batch, "cuda")
         s.set_stages(batch.B, batch.N, **t)
         s.solve(batch.B)

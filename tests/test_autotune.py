@@ -43,3 +43,10 @@ def test_library_defaults_match_the_c_defaults():
     assert A.library_defaults(13, 2, 6) == {"check_start": 32, "check_every": 20, "refine_alpha": 0.001,
                                             "rho": 300.0, "refine_steps": 4}
     assert A.library_defaults(9, 2, 6) == A.LIBRARY_DEFAULTS
+
+
+def test_launch_shapes_join_the_grid():
+    grid = {"rho": (100.0,), "horizon_classes": ((), (10,), (10, 20))}
+    c = A.candidates(grid)
+    assert [x["horizon_classes"] for x in c] == [(), (10,), (10, 20)]
+    assert all(x["rho"] == 100.0 for x in c)

@@ -22,3 +22,19 @@ def test_autotune_small_grid():
     best = res["best"]
     assert best is not None and best["certified"] == batch.B
     assert best["ms"] <= res["default"]["ms"]
+
+
+def test_autotune_horizon_classes():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_05687_b300 import autotune as A
+    batch = W.generate(W.rl_scale_walking(B=512, N=30, seed=63, horizon_min=5))
+    grid = {"rho": (100.0,), "horizon_classes": ((), (10, 20))}
+    res = A.autotune(batch, grid=grid, limit=None, trials=3)
+    assert [t["config"]["horizon_classes"] for t in res["table"]] == [(), (10, 20)]
+    # the classes change the launch shapes, never which instances certify
+    assert res["table"][0]["certified"] == res["table"][1]["certified"] == batch.B
+    print("ms without / with classes", res["table"][0]["ms"], res["table"][1]["ms"])
