@@ -40,6 +40,8 @@ def library_defaults(nx: int, n_contacts: int, contact_dim: int, names: Iterable
     cfg = pinmpc.default_config(nx, n_contacts, contact_dim, 1, 1)
     out = {}
     for n in names:
+        if not hasattr(cfg, n):  # a launch-shape key, not a configuration field
+            continue
         v = getattr(cfg, n)
         out[n] = float(f"{v:.6g}") if isinstance(v, float) else v
     return out

@@ -50,3 +50,10 @@ def test_launch_shapes_join_the_grid():
     c = A.candidates(grid)
     assert [x["horizon_classes"] for x in c] == [(), (10,), (10, 20)]
     assert all(x["rho"] == 100.0 for x in c)
+
+
+def test_library_defaults_skip_launch_shape_keys():
+    import __graft_entry__
+    __graft_entry__.build()
+    d = A.library_defaults(13, 8, 3, ("rho", "horizon_classes"))
+    assert d == {"rho": 100.0}
