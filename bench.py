@@ -546,6 +546,8 @@ def run_gpu(args):
         fsrv = BatchServer(pool, fb.nx, fb.nc, fb.contact_dim, B_max=8192, N=nf, n_handles=SERVE_HANDLES,
                            warm_shift=1, horizon_classes=pinmpc.horizon_classes_for(nf), max_iter=args.max_iter)
         fleet = fleet_load(fsrv, hz=50.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 3)
+        # below capacity: the same fleet ticking at 10 Hz (655k requests/s offered)
+        fleet["at_10hz"] = fleet_load(fsrv, hz=10.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 4)
         fleet.update(warm_loads=fsrv.warm_loads, batches=fsrv.batches,
                      workload="65536 envs x 50 Hz (walking, 8 point contacts), horizons {10,20,30}, stage stride 30, "
                               "Poisson resets 0.5/s/env, warm shift 1; 8192 distinct instances tiled 8x; "
