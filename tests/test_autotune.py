@@ -57,3 +57,12 @@ def test_library_defaults_skip_launch_shape_keys():
     __graft_entry__.build()
     d = A.library_defaults(13, 8, 3, ("rho", "horizon_classes"))
     assert d == {"rho": 100.0}
+
+
+def test_ragged_class_sets_below_the_stride():
+    from paper_2606_05687_b300 import pinmpc
+    assert pinmpc.horizon_classes_for(10) == []
+    assert pinmpc.horizon_classes_for(20) == [10]
+    assert pinmpc.horizon_classes_for(30) == [10, 20]
+    assert pinmpc.horizon_classes_for(40) == [10, 20, 32]
+    assert pinmpc.horizon_classes_for(64) == [10, 20, 32]
