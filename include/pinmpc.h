@@ -52,7 +52,7 @@ typedef enum mpc_status {
     MPC_ERR_OOM = 2,          /* workspace does not fit the memory budget / device */
     MPC_ERR_CUDA = 3,         /* a CUDA call failed; see mpc_last_error */
     MPC_ERR_STATE = 4,        /* call out of order (e.g. solve before set_stages) */
-    MPC_ERR_UNSUPPORTED = 5   /* valid request outside this build's limits */
+    MPC_ERR_UNSUPPORTED = 5   /* valid request outside the compiled shapes or limits */
 } mpc_status;
 
 /* Per-instance result codes written by mpc_get_traj's status array. */
@@ -69,7 +69,7 @@ enum {
 
 /* Solver configuration; fill with mpc_default_config then adjust. */
 typedef struct mpc_config {
-    int32_t nx;            /* state dimension (13 in this build) */
+    int32_t nx;            /* state dimension: 13, or 9 (the 9-state centroidal model) */
     int32_t n_contacts;    /* contacts per stage: 8 (contact_dim 3) or 2 (contact_dim 6) */
     int32_t contact_dim;   /* 3 or 6; nu = n_contacts * contact_dim */
     int32_t B_max;         /* largest batch passed to mpc_set_stages */

@@ -20,7 +20,7 @@ using namespace pinmpc;
 
 namespace {
 
-// Shapes this build is compiled for: (nx, nu, contact_dim).
+// Shapes the library is compiled for: (nx, nu, contact_dim).
 using D24 = Dims<13, 24, 3>;  // 8 point contacts (4 corners per foot)
 using D12 = Dims<13, 12, 6>;  // 2 foot wrenches
 // the 9-state centroidal model xi = [c, l_G, k_G] with the same contact models
