@@ -1115,32 +1115,36 @@ __global__ void pack_kernel(PackArgs a) {
     float* rec = a.rec + (size_t)b * a.irec;
     const float sg = a.sigma, isg = 1.0f / a.sigma;
     const size_t sb = (size_t)b * N;
+    // inputs through the read-only path (they never alias the records), so
+    // the unrolled copy loops keep several loads in flight per thread
+#pragma unroll 4
     for (int e = tid; e < N * NX * NX; e += nthr) {
         const int k = e / (NX * NX), r = e % (NX * NX);
-        rec[k * D::SREC + D::oA + r] = a.A[sb * NX * NX + e];
+        rec[k * D::SREC + D::oA + r] = __ldg(a.A + sb * NX * NX + e);
     }
+#pragma unroll 4
     for (int e = tid; e < N * NX * NU; e += nthr) {
         const int k = e / (NX * NU), r = e % (NX * NU);
-        rec[k * D::SREC + D::oB + r] = sg * a.Bm[sb * NX * NU + e];
+        rec[k * D::SREC + D::oB + r] = sg * __ldg(a.Bm + sb * NX * NU + e);
     }
     for (int e = tid; e < N * NX; e += nthr) {
         const int k = e / NX, r = e % NX;
         float* s = rec + k * D::SREC;
-        s[D::oE + r] = a.e ? a.e[sb * NX + e] : 0.0f;
-        s[D::oQ + r] = a.Q[sb * NX + e];
-        s[D::oRY + r] = a.ry[sb * NX + e];
+        s[D::oE + r] = a.e ? __ldg(a.e + sb * NX + e) : 0.0f;
+        s[D::oQ + r] = __ldg(a.Q + sb * NX + e);
+        s[D::oRY + r] = __ldg(a.ry + sb * NX + e);
     }
     for (int e = tid; e < N * NU; e += nthr) {
         const int k = e / NU, r = e % NU;
         float* s = rec + k * D::SREC;
-        s[D::oR + r] = sg * sg * a.R[sb * NU + e];
-        s[D::oRU + r] = a.ru ? a.ru[sb * NU + e] * isg : 0.0f;
+        s[D::oR + r] = sg * sg * __ldg(a.R + sb * NU + e);
+        s[D::oRU + r] = a.ru ? __ldg(a.ru + sb * NU + e) * isg : 0.0f;
     }
     for (int e = tid; e < N * NC; e += nthr) {
         const int k = e / NC, r = e % NC;
         float* s = rec + k * D::SREC;
-        s[D::oMU + r] = a.mu[sb * NC + e];
-        s[D::oFM + r] = a.fmax[sb * NC + e] * isg;
+        s[D::oMU + r] = __ldg(a.mu + sb * NC + e);
+        s[D::oFM + r] = __ldg(a.fmax + sb * NC + e) * isg;
     }
     for (int k = tid; k < N; k += nthr) {
         float* s = rec + k * D::SREC;
