@@ -62,9 +62,9 @@ KERNEL_HEADERS = {
 }
 MEASURED_TRAFFIC = {
     # profiles/polish_cta_kernel_walking_B4096_N20.md: round-0 launch (all 4096 instances)
-    "polish:4000f8cef5a403b9": 290644736,
+    "polish:797eff1fed1d6180": 290403072,
     # profiles/round2_kernel_walking_B4096_N20.md: round-0 launch
-    "round:cd66cca8787595f5": 439440128,
+    "round:9b74afa9b31dcda1": 437087232,
 }
 
 
