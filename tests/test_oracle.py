@@ -92,6 +92,19 @@ def test_unconstrained_equals_lqr(maker, e_scale):
         assert np.abs(sol.xi - xs).max() <= 1e-9 * max(1.0, np.abs(xs).max())
 
 
+@pytest.mark.parametrize("maker,N", [(W.small_centroidal, 40), (W.rl_scale_walking, 64)])
+def test_unconstrained_equals_lqr_long_horizons(maker, N):
+    """The same closed-form pin at the long horizons the two-CTA round serves."""
+    b = W.generate(maker(B=1, N=N, schedule="all_stance", e_scale=0.05, seed=12))
+    inst = standing_interior(qp.instance(b, 0))
+    inst.ru[:, 0] += 3.0
+    xs, us = lqr_tracking(inst)
+    assert strictly_inside(inst, us), "pin setup must leave every face inactive"
+    sol = qp.solve_instance(inst)
+    assert np.abs(sol.u - us).max() <= 1e-8 * np.abs(us).max()
+    assert np.abs(sol.xi - xs).max() <= 1e-8 * max(1.0, np.abs(xs).max())
+
+
 def test_planted_mistakes_fail_lqr_pin(monkeypatch):
     """A dropped offset e_k or a transposed A_k in the oracle's condensing must
     make the LQR pin fail (the pin is sensitive to them)."""
