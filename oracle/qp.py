@@ -23,7 +23,9 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-from paper_2606_05687_b300.workload import Batch, cone_coefficients
+from paper_2606_05687_b300.workload import Batch
+
+from . import project as _project
 
 
 @dataclasses.dataclass
@@ -72,26 +74,9 @@ def instance(batch: Batch, b: int) -> Instance:
 
 def contact_faces(contact_dim: int, mu: float, fmax: float):
     """Rows (G_i, h_i) of the inequalities G_i u_i <= h_i of one stance contact,
-    u_i its contact_dim components: for each tangential j, +t_j - c_j n <= 0
-    and -t_j - c_j n <= 0; then -n <= 0 and n <= n_max."""
-    tang, coef, nrm = cone_coefficients(contact_dim, mu)
-    rows, rhs = [], []
-    for j, c in zip(tang, coef):
-        for sgn in (1.0, -1.0):
-            g = np.zeros(contact_dim)
-            g[j] = sgn
-            g[nrm] = -c
-            rows.append(g)
-            rhs.append(0.0)
-    g = np.zeros(contact_dim)
-    g[nrm] = -1.0
-    rows.append(g)
-    rhs.append(0.0)
-    g = np.zeros(contact_dim)
-    g[nrm] = 1.0
-    rows.append(g)
-    rhs.append(fmax)
-    return np.array(rows), np.array(rhs)
+    u_i its contact_dim components (oracle.project.faces: for each tangential j,
+    +t_j - c_j n <= 0 and -t_j - c_j n <= 0; then -n <= 0 and n <= n_max)."""
+    return _project.faces(contact_dim, mu, fmax)
 
 
 def condense(inst: Instance):

@@ -432,23 +432,3 @@ def _centroidal9(spec, stack, psi, contact_stance, nb, N, dt):
     xi0[:, 6:9] = spec.ref_noise * x0n[:, 6:9]
     nominal = {"cbar": cbar, "lever": lever, "fbar_sum": Fbar}
     return A, Bm, e, Q, ry, xi0, nominal
-
-
-def cone_coefficients(contact_dim: int, mu: float) -> tuple[list[int], list[float], int]:
-    """Tangential component indices, their cone coefficients c_j, and the
-    normal-component index of one contact's generalized pyramid
-    {(t, n): |t_j| <= c_j n, 0 <= n <= n_max}.
-
-    3-D point force (f_x, f_y, f_z): the 4-face friction pyramid, c = (mu, mu).
-    6-D foot wrench (f, tau): friction on f_x, f_y; centre of pressure inside
-    the foot, |tau_x| <= d_y f_z and |tau_y| <= d_x f_z; yaw torque
-    |tau_z| <= mu*min(d_x, d_y) f_z -- a separable inner approximation of the
-    contact wrench cone the paper names in Sec. II-B.
-    This is set geometry (an input description), shared by both solvers.
-    """
-    if contact_dim == 3:
-        return [0, 1], [mu, mu], 2
-    if contact_dim == 6:
-        dx, dy = FOOT_HALF_LENGTH, FOOT_HALF_WIDTH
-        return [0, 1, 3, 4, 5], [mu, mu, dy, dx, mu * min(dx, dy)], 2
-    raise ValueError("contact_dim must be 3 or 6")

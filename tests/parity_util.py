@@ -81,21 +81,16 @@ def dynamics_residual(batch, out):
 
 def cone_violation(batch, out):
     """max normalised face violation on stance contacts and max |u| on swing contacts."""
-    from paper_2606_05687_b300.workload import cone_coefficients
+    from oracle.project import cone
     cd = batch.contact_dim
     u = out["u"].astype(np.float64).reshape(batch.B, batch.N, batch.nc, cd)
     st = batch.stance()
     fmax = batch.fmax.astype(np.float64)
     mu = batch.mu.astype(np.float64)
-    tang, _, nrm = cone_coefficients(cd, 1.0)
+    tang, coefs, nrm = cone(cd, mu)
     n = u[..., nrm]
     worst = np.maximum(-n, n - fmax)
-    for j, t in enumerate(tang):
-        if cd == 3 or j < 2:
-            coef = mu
-        else:
-            coef = np.full_like(mu, cone_coefficients(cd, 1.0)[1][j]) if j < 4 else mu * min(
-                cone_coefficients(cd, 1.0)[1][2], cone_coefficients(cd, 1.0)[1][3])
+    for t, coef in zip(tang, coefs):
         worst = np.maximum(worst, np.abs(u[..., t]) - coef * n)
     worst = np.where(st, worst / (1.0 + fmax), 0.0)
     swing = np.where(~st[..., None], np.abs(u), 0.0).max()
