@@ -37,6 +37,7 @@ B_BENCH, N_BENCH, SEED = 4096, 20, 1002
 INFLIGHT = 3  # batches in flight on separate handles and streams (--inflight)
 SERVE_HANDLES = 4  # handles of the served-latency leg (requests answered as their round ends)
 KKT_TOL = 1e-5
+PLAIN_ITERS = 200  # the paper's iteration budget (plain_admm leg)
 # FP32 peak derived from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
@@ -61,9 +62,9 @@ KERNEL_HEADERS = {
     "polish": ("dims.cuh", "solve.cuh", "polish.cuh", "polish_cta.cuh"),
 }
 MEASURED_TRAFFIC = {
-    # profiles/polish_cta_kernel_walking_B4096_N20.md: round-0 launch (all 4096 instances)
+    # the polish kernel's round-0 launch (all 4096 instances), one ncu capture
     "polish:797eff1fed1d6180": 290403072,
-    # profiles/round2_kernel_walking_B4096_N20.md: round-0 launch
+    # the round kernel's round-0 launch, one ncu capture
     "round:9b74afa9b31dcda1": 437087232,
 }
 
@@ -253,15 +254,19 @@ def run_reference(args):
     if rank != 0:
         return
     cores = host_cores()
-    per_step, total = [], 0
+    per_step, step_s, total = [], [], 0
     for s in range(args.warmup + args.steps):
         n, el, _, _ = oracle_sample(args.ref_seconds, cores, start=64 * s)
         if s >= args.warmup:
             per_step.append(n / el)
+            step_s.append(el)
             total += n
     v = statistics.mean(per_step)
+    # a step is a bounded sample of the workload: ms_per_step is the time of
+    # what each step actually solved (total / steps instances, not all 4096)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B_BENCH / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(step_s),
+            "instances_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": B_BENCH, "horizon": N_BENCH, "seed": SEED},
@@ -593,6 +598,58 @@ def run_gpu(args):
                               "horizons U{5..40}, stage stride 40, horizon classes (10, 20, 32, 40), both shapes solved concurrently "
                               "(inputs resident)"}
 
+    plain = None
+    if not args.device_only:
+        # the paper's method on its own: ADMM with acceleration and restart, no
+        # polish, the paper's budget of 200 iterations, the certificate checked
+        # every 10 iterations (an instance stops once its KKT residual is
+        # <= 1e-5); same batch, inputs resident, one batch in flight; each
+        # launch timed by the library's CUDA events
+        pa = pinmpc.solver_for(batch, polish=0, max_iter=PLAIN_ITERS, check_start=10, check_every=10,
+                               check_growth=1.0, kkt_tol=KKT_TOL)
+        po = device_outputs()
+        s0 = streams[0]
+
+        def plain_step():
+            pa.set_stages(B, N, **t, stream=s0)
+            pa.solve(B, stream=s0)
+            pa.get_traj(po["xi"], po["u"], po["st"], po["it"], po["kk"], None, stream=s0)
+
+        plain_step()
+        barrier()
+        pa.set_kernel_timing(True)
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s0)
+        for _ in range(reps):
+            plain_step()
+        e1.record(s0)
+        barrier()
+        p_ms = e0.elapsed_time(e1) / reps
+        pk = pa.kernel_times(reset=True)
+        pa.set_kernel_timing(False)
+        p_st, p_it, p_kk = po["st"].cpu().numpy(), po["it"].cpu().numpy(), po["kk"].cpu().numpy()
+        p_fl = kernel_flops(p_it, np.zeros(B), np.zeros(B), batch.horizon)
+        r_ms, r_n = pk["round"]
+        plain = {"solves_per_s": B / (p_ms / 1e3), "ms_per_solve": p_ms,
+                 "certified_1e-5": int(((p_st == 0) & (p_kk <= 1e-5)).sum()),
+                 "kkt_le_1e-4": int((p_kk <= 1e-4).sum()),
+                 "certified_per_s": int(((p_st == 0) & (p_kk <= 1e-5)).sum()) / (p_ms / 1e3),
+                 "kkt": {"p50": float(np.median(p_kk)), "p99": float(np.percentile(p_kk, 99)), "max": float(p_kk.max())},
+                 "iters_mean": float(p_it.mean()),
+                 "round_kernel": {"launches": r_n, "ms_per_launch": r_ms / max(r_n, 1),
+                                  "share": r_ms / max(sum(m for m, _ in pk.values()), 1e-9),
+                                  "achieved_tflops": p_fl["round"] * reps / (r_ms / 1e3) / 1e12 if r_ms else None},
+                 "what": f"polish off, fast ADMM with restart, cap {PLAIN_ITERS} iterations (the paper's budget), "
+                         "certificate every 10 iterations at 1e-5; one batch in flight"}
+        if refs:
+            u_p = po["u"].cpu().numpy().astype(np.float64)
+            e_p = [np.abs(u_p[b_, :int(batch.horizon[b_])] - u_r).max() / max(np.abs(u_r).max(), 1e-9)
+                   for b_, (_, u_r) in refs.items()]
+            plain["oracle_error"] = {"instances": len(e_p), "u_rel_p50": float(np.median(e_p)),
+                                     "u_rel_max": float(np.max(e_p))}
+        pa.close()
+
     if rank != 0:
         return
     # roofline of the dominant kernel from the live per-kernel times (each
@@ -641,6 +698,7 @@ def run_gpu(args):
         "graph": graph,
         "uneven": uneven,
         "fleet": fleet,
+        "plain_admm": plain,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),

@@ -96,7 +96,17 @@ typedef struct mpc_config {
     float foot_half_width; /* d_y of the wrench cone (contact_dim 6) */
     uint64_t mem_budget;   /* device bytes this handle may allocate; 0 = no limit */
     int32_t device;        /* CUDA device ordinal */
+    int32_t precision;     /* operands of the per-stage Gram products behind the ADMM caches
+                              (B_k B_k' and T_k D'^-1 T_k' with T_k = [A_k B_k], Sec. III's
+                              J_k and H_k): MPC_PREC_FP32 (default), or MPC_PREC_TF32 /
+                              MPC_PREC_BF16 on the tensor cores with FP32 accumulation.  The
+                              iteration, the polish and the certificate stay FP32: the
+                              certified KKT bound holds for every mode (the polish and its
+                              refinement recover what the rounded caches lose) */
 } mpc_config;
+
+/* mpc_config.precision */
+enum { MPC_PREC_FP32 = 0, MPC_PREC_TF32 = 1, MPC_PREC_BF16 = 2 };
 
 /* Stage data of one batch.  Arrays are instance-major with stage stride N. */
 typedef struct mpc_stage_view {
@@ -243,10 +253,17 @@ mpc_status mpc_set_round_events(mpc_handle* h, void* const* events, int32_t n);
  *     start the next mpc_solve_batch from row idx[b] of `store` (saved at
  *     the same N); the others start cold.  Put the environments with saved
  *     state first in the batch.
- * `store` is device memory of `rows` rows owned by the caller; indices
- * outside [0, rows) are not written (save) or start cold (load); both calls
- * are asynchronous on `stream`. */
+ * `store` (`rows` rows) and `idx` ([B] int32, or NULL) are caller-owned
+ * device memory of the handle's device; host or other-device pointers are
+ * rejected with MPC_ERR_INVALID_ARG before anything is launched.  Indices
+ * outside [0, rows) are not written (save) or start cold (load).  A save
+ * whose idx names one row for several slots writes that row from all of them
+ * at once (a mix): give -1 to every slot but one.  Both calls are
+ * asynchronous on `stream`. */
 int64_t mpc_state_floats(mpc_handle* h, int32_t N);
+/* mpc_state_floats for cfg's shape without a handle (host only; 0 for an
+ * unbuilt shape or N outside [1, 64]): for sizing a store by a memory budget. */
+int64_t mpc_state_floats_estimate(const mpc_config* cfg, int32_t N);
 mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32_t rows, int32_t B, int32_t shift,
                           void* stream);
 mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx, int32_t rows, int32_t B,
@@ -296,8 +313,10 @@ mpc_status mpc_get_graph_stats(mpc_handle* h, int64_t* captures, int64_t* replay
  * paper; this is a deployment aid).  For callers that may not allocate: code
  * inside someone else's captured CUDA graph, a simulator step that owns a
  * fixed memory pool and forbids cudaMalloc on its hot path, or a real-time
- * loop that must stay clear of the allocator.  The caller passes device
- * buffers only (host pointers are rejected: staging them would allocate):
+ * loop that must stay clear of the allocator.  It runs on the calling
+ * thread's current CUDA device, and the caller passes buffers of that device
+ * only (host pointers and other GPUs' memory are rejected: staging them
+ * would allocate):
  * the stage view as for mpc_set_stages, and the outputs xi [B][N][nx],
  * u [B][N][nu], status, iters, kkt [B] as for mpc_get_traj.  The solver's
  * scratch (packed records, face bits, polish counts) is a fixed 8 MiB static
@@ -326,6 +345,16 @@ const char* mpc_last_error(mpc_handle* h);
 
 /* Bytes of device memory the handle owns. */
 uint64_t mpc_workspace_bytes(mpc_handle* h);
+
+/* Device bytes mpc_create would allocate for cfg (the value
+ * mpc_workspace_bytes reports right after creation), computed on the host
+ * without a device and without allocating, so that a caller can admit work
+ * by a device-memory budget before creating handles.  A handle that later
+ * receives host-memory inputs adds a staging buffer of the batch's input size
+ * on first use.  No counterpart in the paper.  MPC_ERR_INVALID_ARG (null
+ * pointers, bad dimensions), MPC_ERR_UNSUPPORTED (shape not built, N_max
+ * above mpc_max_horizon's limit). */
+mpc_status mpc_workspace_estimate(const mpc_config* cfg, uint64_t* bytes);
 
 #ifdef __cplusplus
 }

@@ -14,6 +14,8 @@
 // stage-iteration touches shared memory only for the vectors other lanes or
 // other stages read.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "polish.cuh"
 #include "tma.cuh"
 
@@ -388,11 +390,34 @@ __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int
     return warp_sum(cm);
 }
 
+// In-place Gauss-Jordan inverse of an SPD matrix held one row per lane pair
+// (row r = lane/2 in lanes 2r, 2r+1; lanes past the last row duplicate it);
+// no pivoting, the matrix is SPD.
+template <class D>
+__device__ __forceinline__ void gj_inverse_rows(int lane, float (&row)[D::NX]) {
+    constexpr int NX = D::NX;
+    const int r = min(lane >> 1, NX - 1);
+#pragma unroll
+    for (int p = 0; p < NX; ++p) {
+        float prow[NX];
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) prow[cc] = __shfl_sync(0xffffffffu, row[cc], 2 * p);
+        const float piv = 1.0f / prow[p];
+        const float fp = row[p] * piv;
+        const bool mine = (r == p);
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) {
+            const float other = (cc == p) ? -fp : fmaf(-fp, prow[cc], row[cc]);
+            const float pivr = (cc == p) ? piv : prow[cc] * piv;
+            row[cc] = mine ? pivr : other;
+        }
+    }
+}
+
 // Row r of  dg I + T diag(d) T'  over the columns i >= i0 of T = [A B] (lane
 // pair (r, h) sums the columns i = i0 + h, i0 + h + 2, ...; the pair's halves
-// are combined), then its in-place Gauss-Jordan inverse (no pivoting: the
-// matrix is SPD).  Rows are held one per lane pair; lanes past the last row
-// duplicate it.
+// are combined), then its in-place Gauss-Jordan inverse.  Rows are held one
+// per lane pair; lanes past the last row duplicate it.
 template <class D>
 __device__ __forceinline__ void gram_inverse(const float* sj, const float* d, float dg, int i0, int lane,
                                              float (&row)[D::NX]) {
@@ -413,21 +438,88 @@ __device__ __forceinline__ void gram_inverse(const float* sj, const float* d, fl
         row[cc] += __shfl_xor_sync(0xffffffffu, row[cc], 1);
         if (cc == r) row[cc] += dg;
     }
+    gj_inverse_rows<D>(lane, row);
+}
+
+// Precision of the factor kernel's Gram products T diag(d) T' (mpc_config.precision).
+enum : int { kPrecFP32 = 0, kPrecTF32 = 1, kPrecBF16 = 2 };
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t to_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x = lo in the low half
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// The same matrix as gram_inverse, with the Gram product on the tensor cores
+// (warp-level mma.sync, FP32 accumulation): TF32 operands (m16n8k8) or BF16
+// operands (m16n8k16).  M = the NX rows of T (padded to 16), N = the same 16
+// (two 8-column tiles), K = the columns i0 .. NB-1 (padded to the MMA's K);
+// A[m][k] = T[m][i0 + k], B[k][n] = d[i0 + k] T[n][i0 + k].  The 16 x 16
+// result goes through the warp's scratch `sg` (16 x 17 floats) into the row
+// layout of the inversion, which stays FP32.
+template <class D, int PREC>
+__device__ __forceinline__ void gram_inverse_mma(const float* sj, const float* d, float dg, int i0, int lane,
+                                                 float* sg, float (&row)[D::NX]) {
+    constexpr int NX = D::NX, NU = D::NU, NB = D::NB, GP = 17;
+    const int g = lane >> 2, t = lane & 3;
+    auto T = [&](int rr, int cc) -> float {
+        if (rr >= NX || cc >= NB) return 0.0f;
+        return cc < NX ? sj[D::oA + rr * NX + cc] : sj[D::oB + rr * NU + cc - NX];
+    };
+    auto dT = [&](int rr, int cc) -> float { return (cc < NB && d) ? d[cc] * T(rr, cc) : T(rr, cc); };
+    float acc[2][4] = {};
+    if constexpr (PREC == kPrecTF32) {
+        for (int c0 = i0; c0 < NB; c0 += 8) {
+            const uint32_t a0 = to_tf32(T(g, c0 + t)), a1 = to_tf32(T(g + 8, c0 + t));
+            const uint32_t a2 = to_tf32(T(g, c0 + t + 4)), a3 = to_tf32(T(g + 8, c0 + t + 4));
 #pragma unroll
-    for (int p = 0; p < NX; ++p) {
-        float prow[NX];
+            for (int nt = 0; nt < 2; ++nt) {
+                const uint32_t b0 = to_tf32(dT(nt * 8 + g, c0 + t)), b1 = to_tf32(dT(nt * 8 + g, c0 + t + 4));
+                asm volatile(
+                    "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                    "{%0,%1,%2,%3};"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            }
+        }
+    } else {
+        for (int c0 = i0; c0 < NB; c0 += 16) {
+            const uint32_t a0 = to_bf16x2(T(g, c0 + 2 * t), T(g, c0 + 2 * t + 1));
+            const uint32_t a1 = to_bf16x2(T(g + 8, c0 + 2 * t), T(g + 8, c0 + 2 * t + 1));
+            const uint32_t a2 = to_bf16x2(T(g, c0 + 2 * t + 8), T(g, c0 + 2 * t + 9));
+            const uint32_t a3 = to_bf16x2(T(g + 8, c0 + 2 * t + 8), T(g + 8, c0 + 2 * t + 9));
 #pragma unroll
-        for (int cc = 0; cc < NX; ++cc) prow[cc] = __shfl_sync(0xffffffffu, row[cc], 2 * p);
-        const float piv = 1.0f / prow[p];
-        const float fp = row[p] * piv;
-        const bool mine = (r == p);
-#pragma unroll
-        for (int cc = 0; cc < NX; ++cc) {
-            const float other = (cc == p) ? -fp : fmaf(-fp, prow[cc], row[cc]);
-            const float pivr = (cc == p) ? piv : prow[cc] * piv;
-            row[cc] = mine ? pivr : other;
+            for (int nt = 0; nt < 2; ++nt) {
+                const int n = nt * 8 + g;
+                const uint32_t b0 = to_bf16x2(dT(n, c0 + 2 * t), dT(n, c0 + 2 * t + 1));
+                const uint32_t b1 = to_bf16x2(dT(n, c0 + 2 * t + 8), dT(n, c0 + 2 * t + 9));
+                asm volatile(
+                    "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                    "{%0,%1,%2,%3};"
+                    : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                    : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            }
         }
     }
+    // accumulator (row g or g + 8, column nt*8 + 2t or + 1) -> sg
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        sg[g * GP + nt * 8 + 2 * t] = acc[nt][0];
+        sg[g * GP + nt * 8 + 2 * t + 1] = acc[nt][1];
+        sg[(g + 8) * GP + nt * 8 + 2 * t] = acc[nt][2];
+        sg[(g + 8) * GP + nt * 8 + 2 * t + 1] = acc[nt][3];
+    }
+    __syncwarp();
+    const int r = min(lane >> 1, NX - 1);
+#pragma unroll
+    for (int cc = 0; cc < NX; ++cc) row[cc] = sg[r * GP + cc] + (cc == r ? dg : 0.0f);
+    __syncwarp();
+    gj_inverse_rows<D>(lane, row);
 }
 
 // Per-stage factors of the ADMM round, one warp per (instance, stage):
@@ -442,15 +534,20 @@ struct FactorArgs {
     float rho;
     float* cache;  // [B][N][2][NX][16]
     int* flags;    // [B], zeroed before the launch
+    int precision; // kPrecFP32 / kPrecTF32 / kPrecBF16: operands of the Gram products
 };
 constexpr int kFactorWarps = 8;
 
-template <class D>
+// PREC selects the Gram products' operands (FP32 on the FMA pipes, or TF32 /
+// BF16 on the tensor cores with FP32 accumulation); the inversions are FP32.
+template <class D, int PREC = kPrecFP32>
 __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a) {
     constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     static_assert(D::SREC % 4 == 0, "records are copied as float4");
+    static_assert(NX <= 16, "the tensor-core Gram covers 16 rows");
     __shared__ __align__(16) float s_rec[kFactorWarps][D::SREC];
     __shared__ __align__(16) float s_d[kFactorWarps][NBP];
+    __shared__ float s_g[PREC == kPrecFP32 ? 1 : kFactorWarps][PREC == kPrecFP32 ? 1 : 16 * 17];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kFactorWarps + warp;
     if (gw >= a.B * a.N) return;  // whole warps leave; the kernel has no CTA barrier
@@ -498,10 +595,18 @@ __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a)
             }
         }
     };
-    gram_inverse<D>(sr, nullptr, 1.0f, NX, lane, row);
+    if constexpr (PREC == kPrecFP32) {
+        gram_inverse<D>(sr, nullptr, 1.0f, NX, lane, row);
+    } else {
+        gram_inverse_mma<D, PREC>(sr, nullptr, 1.0f, NX, lane, s_g[warp], row);
+    }
     store(0);
     if (j >= 1) {
-        gram_inverse<D>(sr, dd, 1.0f / a.rho, 0, lane, row);
+        if constexpr (PREC == kPrecFP32) {
+            gram_inverse<D>(sr, dd, 1.0f / a.rho, 0, lane, row);
+        } else {
+            gram_inverse_mma<D, PREC>(sr, dd, 1.0f / a.rho, 0, lane, s_g[warp], row);
+        }
         store(1);
     }
 }
@@ -806,10 +911,14 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
             if (bn >= 0 && threadIdx.x == 0) round_fetch<D, CAPPED>(a, smem, bar, bn, cur ^ 1);
             const bool ok = __syncthreads_and(mbar_wait(&bar[cur], (uint32_t)(it >> 1) & 1u));
             if (!ok) {
-                // the copies did not arrive: report this instance, let the other
-                // buffer's copies land (bounded), and stop taking work
-                if (bn >= 0) mbar_wait(&bar[cur ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+                // the copies did not arrive in time: report this instance and the
+                // next one already taken from the list, give every copy issued
+                // into this CTA's shared memory another bounded wait to land,
+                // and stop taking work (the other CTAs drain the list)
                 round_fail<D>(a, b, kTimeout);
+                if (bn >= 0) round_fail<D>(a, bn, kTimeout);
+                mbar_wait(&bar[cur], (uint32_t)(it >> 1) & 1u);
+                if (bn >= 0) mbar_wait(&bar[cur ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
                 return;
             }
         }

@@ -64,7 +64,10 @@ int cache_floats_t(int N) { return RoundSmem<D>::cache_floats(N); }
 template <class D>
 void launch_factor_t(const FactorArgs& a, cudaStream_t s) {
     const int warps = a.B * a.N;
-    factor_kernel<D><<<(warps + kFactorWarps - 1) / kFactorWarps, 32 * kFactorWarps, 0, s>>>(a);
+    const int grid = (warps + kFactorWarps - 1) / kFactorWarps;
+    if (a.precision == kPrecTF32) factor_kernel<D, kPrecTF32><<<grid, 32 * kFactorWarps, 0, s>>>(a);
+    else if (a.precision == kPrecBF16) factor_kernel<D, kPrecBF16><<<grid, 32 * kFactorWarps, 0, s>>>(a);
+    else factor_kernel<D><<<grid, 32 * kFactorWarps, 0, s>>>(a);
 }
 template <class D>
 cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
@@ -346,6 +349,17 @@ static bool is_host_pointer(const void* p) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
+// Device (or managed) memory of `device`: what a kernel of this library may
+// dereference directly.
+static bool is_device_memory(const void* p, int device) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice && at.device == device) || at.type == cudaMemoryTypeManaged;
+}
+
 // Host memory the CUDA runtime does not know (not page-locked): a copy into
 // it is complete only once the stream has reached it.
 static bool is_pageable_pointer(const void* p) {
@@ -358,7 +372,37 @@ static bool is_pageable_pointer(const void* p) {
     return at.type == cudaMemoryTypeUnregistered;
 }
 
+// Device bytes mpc_create allocates for cfg (records, outputs, factor cache,
+// ADMM state, face words, work lists, polish gains); the host-input staging
+// buffer is allocated later, on the first set_stages from host memory.
+static uint64_t workspace_bytes_of(const mpc_config& c, const Shape& sh) {
+    const size_t B = (size_t)c.B_max, N = (size_t)c.N_max;
+    const size_t nc = (size_t)c.n_contacts, nu = nc * (size_t)c.contact_dim;
+    const size_t irec = (size_t)instance_record_floats(sh.srec, sh.tail, c.N_max);
+    const size_t rec_b = B * irec * sizeof(float);
+    const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * nu * sizeof(float);
+    const size_t small_b = B * (4 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
+    const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
+    const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
+    const size_t modes_b = B * N * nc * sizeof(uint32_t);
+    const size_t kst_b = B * N * nu * (c.nx + 1) * sizeof(float);
+    const size_t round_b = cache_b + state_b + 2 * modes_b + (2 + 2 * kMaxClasses) * B * sizeof(int) +
+                           3 * kMaxClasses * sizeof(int) + kst_b;
+    return rec_b + xi_b + u_b + small_b + round_b;
+}
+
 extern "C" {
+
+mpc_status mpc_workspace_estimate(const mpc_config* cfg, uint64_t* bytes) {
+    if (!cfg || !bytes) return MPC_ERR_INVALID_ARG;
+    Shape sh;
+    if (cfg->contact_dim != 3 && cfg->contact_dim != 6) return MPC_ERR_INVALID_ARG;
+    if (!pick_shape(cfg->nx, cfg->n_contacts, cfg->contact_dim, &sh)) return MPC_ERR_UNSUPPORTED;
+    if (cfg->B_max < 1 || cfg->N_max < 1) return MPC_ERR_INVALID_ARG;
+    if (cfg->N_max > kClusterMaxN) return MPC_ERR_UNSUPPORTED;
+    *bytes = workspace_bytes_of(*cfg, sh);
+    return MPC_OK;
+}
 
 mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, int32_t contact_dim,
                               int32_t B_max, int32_t N_max) {
@@ -385,6 +429,7 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->foot_half_width = 0.05f;
     cfg->mem_budget = 0;
     cfg->device = 0;
+    cfg->precision = MPC_PREC_FP32;
     if (nx == 13 && contact_dim == 6) {
         // foot wrenches on the 13-state model: a stiffer penalty, a later
         // first check and finer, longer refinement (measured: 2.3-6x faster,
@@ -425,7 +470,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||
         c.check_every < 1 || c.check_start < 1 || !(c.check_growth >= 1.0f) || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
         !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f) || c.refine_steps < 0 ||
-        !(c.refine_alpha > 0.0f))
+        !(c.refine_alpha > 0.0f) || c.precision < MPC_PREC_FP32 || c.precision > MPC_PREC_BF16)
         return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
     if (c.N_max > kClusterMaxN)
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds %d stages (one warp per stage, two CTAs)",
@@ -463,13 +508,11 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t B = (size_t)c.B_max, N = (size_t)c.N_max;
     const size_t rec_b = B * h->irec * sizeof(float);
     const size_t xi_b = B * N * c.nx * sizeof(float), u_b = B * N * h->nu * sizeof(float);
-    const size_t small_b = B * (4 * sizeof(int) + sizeof(float)) + B * N * sizeof(unsigned long long);
     const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
     const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
-    const size_t round_b = cache_b + state_b + 2 * modes_b + (2 + 2 * kMaxClasses) * B * sizeof(int) + sizeof(int) + kst_b;
-    h->bytes = rec_b + xi_b + u_b + small_b + round_b;
+    h->bytes = workspace_bytes_of(c, sh);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }
     if ((c.mem_budget && h->bytes > c.mem_budget) || h->bytes > free_b) {
@@ -650,7 +693,7 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
     {
         FactorArgs fa{};
         fa.rec = h->rec; fa.irec = h->irec; fa.n_rec = c.N_max; fa.N = h->N_set; fa.B = B;
-        fa.rho = c.rho; fa.cache = h->cache; fa.flags = h->flags;
+        fa.rho = c.rho; fa.cache = h->cache; fa.flags = h->flags; fa.precision = c.precision;
         if ((e = timed_launch(h, kClassFactor, st, [&] { h->shape.launch_factor(fa, st); })) != cudaSuccess)
             return cuda_fail(h, e, "factor kernel launch");
     }
@@ -872,6 +915,12 @@ int64_t mpc_state_floats(mpc_handle* h, int32_t N) {
     return h->shape.state_floats(N);
 }
 
+int64_t mpc_state_floats_estimate(const mpc_config* cfg, int32_t N) {
+    Shape sh;
+    if (!cfg || N < 1 || N > kClusterMaxN || !pick_shape(cfg->nx, cfg->n_contacts, cfg->contact_dim, &sh)) return 0;
+    return sh.state_floats(N);
+}
+
 mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32_t rows, int32_t B, int32_t shift,
                           void* stream) {
     if (!h) return MPC_ERR_INVALID_ARG;
@@ -881,6 +930,8 @@ mpc_status mpc_save_state(mpc_handle* h, float* store, const int32_t* idx, int32
     if (shift < 0 || shift >= h->N_set) return fail(h, MPC_ERR_INVALID_ARG, "shift=%d outside [0, N=%d)", shift, h->N_set);
     cudaError_t e = cudaSetDevice(h->cfg.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!is_device_memory(store, h->cfg.device) || (idx && !is_device_memory(idx, h->cfg.device)))
+        return fail(h, MPC_ERR_INVALID_ARG, "store and idx must be device memory of the handle's device");
     const int smem = h->shape.state_floats(h->N_set) * (int)sizeof(float);
     if (smem > 48 * 1024 && (e = h->shape.set_state_copy_attr(smem)) != cudaSuccess)
         return cuda_fail(h, e, "cudaFuncSetAttribute");
@@ -898,6 +949,8 @@ mpc_status mpc_load_state(mpc_handle* h, const float* store, const int32_t* idx,
     if (B < 1 || B > h->B_set) return fail(h, MPC_ERR_INVALID_ARG, "B=%d outside [1, %d]", B, h->B_set);
     cudaError_t e = cudaSetDevice(h->cfg.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!is_device_memory(store, h->cfg.device) || (idx && !is_device_memory(idx, h->cfg.device)))
+        return fail(h, MPC_ERR_INVALID_ARG, "store and idx must be device memory of the handle's device");
     const int smem = h->shape.state_floats(h->N_set) * (int)sizeof(float);
     if (smem > 48 * 1024 && (e = h->shape.set_state_copy_attr(smem)) != cudaSuccess)
         return cuda_fail(h, e, "cudaFuncSetAttribute");

@@ -37,13 +37,15 @@ mpc_status fail(mpc_status st, const std::string& msg) {
     return st;
 }
 
-bool is_device_pointer(const void* p) {
+// Device memory of `device` (or managed memory): a buffer of another GPU
+// would be read across the interconnect, or fault without peer access.
+bool is_device_pointer(const void* p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice && at.device == device) || at.type == cudaMemoryTypeManaged;
 }
 
 template <class D>
@@ -135,14 +137,22 @@ mpc_status mpc_solve_noalloc(const mpc_config* cfg, const mpc_stage_view* v, flo
         c.check_start < 1 || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) || c.refine_steps < 0 ||
         !(c.refine_alpha > 0.0f))
         return fail(MPC_ERR_INVALID_ARG, "invalid solver parameter");
+    if (c.precision != MPC_PREC_FP32)
+        return fail(MPC_ERR_UNSUPPORTED, "the no-allocation solver runs FP32 only (precision must be MPC_PREC_FP32)");
     if (v->B < 1 || v->N < 1 || v->N > 32) return fail(MPC_ERR_INVALID_ARG, "B must be >= 1 and N in [1, 32]");
     if (!v->A || !v->Bm || !v->Q || !v->R || !v->ry || !v->mu || !v->fmax || !v->mask || !v->xi0)
         return fail(MPC_ERR_INVALID_ARG, "a required stage array is NULL");
     const void* ptrs[] = {v->A, v->Bm, v->e, v->Q, v->R, v->ry, v->ru, v->mu, v->fmax, v->mask, v->xi0,
                           v->u_prev, v->horizon, xi, u, status, iters, kkt};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MPC_ERR_CUDA, "no current CUDA device");
+    }
     for (const void* p : ptrs)
-        if (p && !is_device_pointer(p))
-            return fail(MPC_ERR_INVALID_ARG, "every buffer must be device memory (staging host data would allocate)");
+        if (p && !is_device_pointer(p, dev))
+            return fail(MPC_ERR_INVALID_ARG,
+                        "every buffer must be device memory of the current device (staging host data would allocate)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (c.nx == 13 && c.contact_dim == 3 && c.n_contacts == 8)
         return run<Dims<13, 24, 3>>(c, *v, xi, u, status, iters, kkt, s, 0);

@@ -9,7 +9,8 @@
 //                a forward rollout;
 //   certificate: costate scan, stationarity, per-contact nonnegative
 //                multipliers (cyclic coordinate descent) and the KKT
-//                residual of Sec. IV's stopping test;
+//                residual this implementation stops on (the paper gives only an
+//                iteration budget);
 //   refinement:  faces re-read from the projection of u - alpha sigma w, then
 //                polish again (at most refine_steps times).
 // Stage records are staged through shared memory with a register prefetch

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpinmpc.so")
 MPC_OK, MPC_ERR_INVALID_ARG, MPC_ERR_OOM, MPC_ERR_CUDA, MPC_ERR_STATE, MPC_ERR_UNSUPPORTED = range(6)
 CONVERGED, MAX_ITER, NONFINITE, BAD_SET, TIMEOUT, BAD_HORIZON = range(6)
 RUNNING = -1  # status of an instance whose solve has not finished it yet
+PREC_FP32, PREC_TF32, PREC_BF16 = range(3)  # mpc_config.precision
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID_ARG", 2: "MPC_ERR_OOM", 3: "MPC_ERR_CUDA",
                 4: "MPC_ERR_STATE", 5: "MPC_ERR_UNSUPPORTED"}
 
@@ -32,7 +33,7 @@ class MpcConfig(ctypes.Structure):
                 ("restart_eta", ctypes.c_float), ("refine_steps", ctypes.c_int32),
                 ("refine_alpha", ctypes.c_float), ("foot_half_length", ctypes.c_float),
                 ("foot_half_width", ctypes.c_float), ("mem_budget", ctypes.c_uint64),
-                ("device", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -109,6 +110,10 @@ def load() -> ctypes.CDLL:
     lib.mpc_last_error.restype = ctypes.c_char_p
     lib.mpc_workspace_bytes.argtypes = [ctypes.c_void_p]
     lib.mpc_workspace_bytes.restype = ctypes.c_uint64
+    lib.mpc_workspace_estimate.argtypes = [ctypes.POINTER(MpcConfig), ctypes.POINTER(ctypes.c_uint64)]
+    lib.mpc_workspace_estimate.restype = ctypes.c_int
+    lib.mpc_state_floats_estimate.argtypes = [ctypes.POINTER(MpcConfig), ctypes.c_int32]
+    lib.mpc_state_floats_estimate.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -131,6 +136,21 @@ def default_config(nx: int, n_contacts: int, contact_dim: int, B_max: int, N_max
             raise AttributeError(f"mpc_config has no field {k!r}")
         setattr(cfg, k, v)
     return cfg
+
+
+def workspace_estimate(cfg: MpcConfig) -> int:
+    """Device bytes mpc_create would allocate for ``cfg`` (host-side, no device)."""
+    lib = load()
+    out = ctypes.c_uint64()
+    st = lib.mpc_workspace_estimate(ctypes.byref(cfg), ctypes.byref(out))
+    if st != MPC_OK:
+        raise MpcError(st, "mpc_workspace_estimate")
+    return int(out.value)
+
+
+def state_floats_estimate(cfg: MpcConfig, N: int) -> int:
+    """Floats of one instance's warm state at stride N for ``cfg``'s shape (no handle)."""
+    return int(load().mpc_state_floats_estimate(ctypes.byref(cfg), int(N)))
 
 
 def _ptr(t) -> Optional[int]:

@@ -26,6 +26,12 @@ request is the environment's next MPC step), environments with a state
 are placed first in their batch, and `reset(envs)` makes the next request
 of those environments cold (a new episode).  Two requests of one
 environment in the same batch both start from its state before the batch.
+A batch that loads a row another handle's batch saved waits for that save
+on the device, so an environment's requests see its states in request
+order whichever handles serve them.  With a device-memory budget the store
+may hold fewer rows than environments; rows are then reclaimed least
+recently used, never while a batch in flight uses them, and an environment
+whose row was reclaimed starts cold.
 """
 from __future__ import annotations
 
@@ -37,6 +43,96 @@ import numpy as np
 from . import pinmpc
 
 STAGE_KEYS = ("A", "Bm", "e", "Q", "R", "ry", "ru", "mu", "fmax", "mask", "xi0", "u_prev", "horizon")
+ALLOC_ROUND = 512  # the device allocator's granule: every tensor is counted rounded up to it
+
+
+def _rounded(nbytes: int) -> int:
+    return -(-int(nbytes) // ALLOC_ROUND) * ALLOC_ROUND
+
+
+def handle_bytes(workspace: int, B_max: int, N: int, nx: int, nu: int, env_input_bytes: Dict[str, int]) -> int:
+    """Device bytes of one server handle: the library workspace, the gathered
+    stage-data buffers (B_max rows of every stage array), the outputs
+    (u, xi, status, kkt) and the index vectors of a batch."""
+    b = workspace
+    b += sum(_rounded(B_max * v) for v in env_input_bytes.values())
+    b += _rounded(B_max * N * nu * 4) + _rounded(B_max * N * nx * 4) + 2 * _rounded(B_max * 4)
+    b += _rounded(B_max * 4) + _rounded(B_max * 8) + _rounded(B_max * 4)  # idx (int32, int64), save idx
+    return b
+
+
+def plan_memory(budget: int, n_env: int, n_handles: int, B_max: int, per_handle, state_row_bytes: int,
+                warm: bool) -> dict:
+    """Admission by a device-memory budget: the most handles (batches in
+    flight, up to ``n_handles``) of the largest batch size (``B_max``, halved
+    while needed) that fit, then as many warm-state rows as fit, up to one
+    per environment.  Every slot of every batch in flight holds a row, so
+    rows >= handles x batch size.  ``per_handle(B)`` gives one handle's
+    bytes at batch size B.  Raises MemoryError if one handle of batch size 1
+    does not fit."""
+    B = max(1, int(B_max))
+    while True:
+        for h in range(max(1, n_handles), 0, -1):
+            used = h * per_handle(B)
+            rows = 0
+            if warm:
+                rows = int(min(n_env, max(0, budget - used - ALLOC_ROUND) // max(state_row_bytes, 1)))
+                if rows < min(n_env, h * B):
+                    continue
+                used += _rounded(rows * state_row_bytes)
+                if used > budget:
+                    continue
+            if used <= budget:
+                return {"handles": h, "B_max": B, "warm_rows": rows, "bytes": used}
+        if B == 1:
+            raise MemoryError(f"one handle of batch size 1 needs {per_handle(1)} B, budget {budget} B")
+        B = max(1, B // 2)
+
+
+class WarmRows:
+    """Rows of the device warm-state store, assigned to environments on
+    demand and reclaimed least recently used first.  A row is pinned while a
+    batch in flight loads or saves it and is never reclaimed then; an
+    environment whose row is reclaimed starts its next request cold."""
+
+    def __init__(self, n_env: int, rows: int):
+        self.row_of = np.full(n_env, -1, np.int64)
+        self.env_of = np.full(rows, -1, np.int64)
+        self.last_use = np.zeros(rows, np.int64)
+        self.pins = np.zeros(rows, np.int64)
+        self.clock = 0
+        self.evicted = 0
+
+    def acquire(self, envs: np.ndarray, has_state: np.ndarray) -> np.ndarray:
+        """Rows for the environments of one batch (pinned); environments whose
+        row had to be taken get has_state cleared."""
+        self.clock += 1
+        rows = self.row_of[envs].copy()
+        need = np.unique(envs[rows < 0])
+        if need.size:
+            free = np.flatnonzero((self.env_of < 0) & (self.pins == 0))
+            if free.size < need.size:
+                cand = np.flatnonzero((self.env_of >= 0) & (self.pins == 0))
+                cand = cand[~np.isin(self.env_of[cand], envs)]
+                take = cand[np.argsort(self.last_use[cand], kind="stable")][:need.size - free.size]
+                if free.size + take.size < need.size:
+                    raise RuntimeError("warm-state rows exhausted: more slots in flight than rows")
+                old = self.env_of[take]
+                self.row_of[old] = -1
+                has_state[old] = False
+                self.env_of[take] = -1
+                self.evicted += take.size
+                free = np.concatenate([free, take])
+            got = free[:need.size]
+            self.env_of[got] = need
+            self.row_of[need] = got
+            rows = self.row_of[envs]
+        self.last_use[rows] = self.clock
+        np.add.at(self.pins, rows, 1)
+        return rows
+
+    def release(self, rows: np.ndarray):
+        np.subtract.at(self.pins, rows, 1)
 
 
 class BatchServer:
@@ -44,6 +140,12 @@ class BatchServer:
 
     ``horizon_classes`` (ascending stage counts) makes each handle run its
     ADMM rounds per horizon class, for pools with ragged horizons.
+    ``mem_budget`` (bytes) admits work by device memory: the number of
+    handles (batches in flight, at most ``n_handles``), the batch size (at
+    most ``B_max``) and the rows of the warm-state store (at most one per
+    environment, reclaimed least recently used when fewer) are chosen by
+    ``plan_memory`` so that every device buffer the server allocates fits the
+    budget (``self.plan``); requests beyond the slots in flight queue.
     ``pool`` holds the stage data of every environment the requests refer to
     (torch tensors on the device, keyed like ``pinmpc.device_inputs``; row e
     is environment e).  ``clock`` returns seconds.  Request r (in submission
@@ -53,13 +155,34 @@ class BatchServer:
 
     def __init__(self, pool: Dict[str, "object"], nx: int, nc: int, contact_dim: int, B_max: int, N: int,
                  n_handles: int = 2, clock: Callable[[], float] = time.perf_counter,
-                 warm_shift: Optional[int] = None, early: bool = True, horizon_classes=None, **overrides):
+                 warm_shift: Optional[int] = None, early: bool = True, horizon_classes=None,
+                 mem_budget: Optional[int] = None, **overrides):
         import torch
         self.torch = torch
         self.pool = pool
-        self.B_max, self.N = B_max, N
         self.clock = clock
         self.device = pool["A"].device
+        n_env = int(pool["A"].shape[0])
+        # admission by device memory: with a budget, the handles (batches in
+        # flight), the batch size and the warm-state rows are sized so that
+        # everything the server allocates on the device fits it; requests
+        # beyond what is in flight wait in the queue, none is dropped
+        self.plan = None
+        warm_rows = n_env
+        if mem_budget is not None:
+            nu = nc * contact_dim
+            env_bytes = {k: int(pool[k][0].numel() * pool[k].element_size()) for k in STAGE_KEYS}
+
+            def per_handle(b):
+                cfg_b = pinmpc.default_config(nx, nc, contact_dim, b, N, **overrides)
+                return handle_bytes(pinmpc.workspace_estimate(cfg_b), b, N, nx, nu, env_bytes)
+
+            row_bytes = 4 * pinmpc.state_floats_estimate(pinmpc.default_config(nx, nc, contact_dim, 1, N, **overrides), N)
+            self.plan = plan_memory(int(mem_budget), n_env, n_handles, B_max, per_handle, row_bytes,
+                                    warm_shift is not None)
+            n_handles, B_max, warm_rows = self.plan["handles"], self.plan["B_max"], self.plan["warm_rows"]
+            self.plan["budget"] = int(mem_budget)
+        self.B_max, self.N = B_max, N
         self.handles = []
         for _ in range(n_handles):
             cfg = pinmpc.default_config(nx, nc, contact_dim, B_max, N, **overrides)
@@ -90,10 +213,15 @@ class BatchServer:
         self.warm_shift = warm_shift
         self.warm_loads = 0
         if warm_shift is not None:
-            n_env = pool["A"].shape[0]
             rows = self.handles[0]["solver"].state_floats(N)
-            self.store = torch.zeros((n_env, rows), dtype=torch.float32, device=self.device)
+            self.store = torch.zeros((warm_rows, rows), dtype=torch.float32, device=self.device)
             self.has_state = np.zeros(n_env, dtype=bool)
+            self.rows = WarmRows(n_env, warm_rows)
+            # handle whose batch last saved each store row (-1: none); a batch
+            # that loads the row waits for that handle's save first
+            self.last_writer = np.full(warm_rows, -1, np.int64)
+            for h in self.handles:
+                h["save_event"] = None
         cap = 1 << 16
         self.env = np.zeros(cap, np.int64)
         self.t_arrival = np.zeros(cap)
@@ -152,22 +280,45 @@ class BatchServer:
             perm = np.argsort(~warm, kind="stable")
             envs = envs[perm]
             n_warm = int(warm.sum())
+        rows = None
+        if self.warm_shift is not None:
+            rows = self.rows.acquire(envs, self.has_state)  # pinned until the batch retires
         with torch.cuda.stream(h["stream"]):
-            idx = torch.from_numpy(envs.astype(np.int32)).to(self.device, non_blocking=True)
-            idx64 = idx.long()
+            idx64 = torch.from_numpy(envs).to(self.device, non_blocking=True)
             for k in STAGE_KEYS:
                 torch.index_select(self.pool[k], 0, idx64, out=h["inputs"][k][:B])
         view = {k: h["inputs"][k][:B] for k in STAGE_KEYS}
         s = h["solver"]
         s.set_stages(B, self.N, **view, stream=h["stream"])
+        me = self.handles.index(h)
+        if self.warm_shift is not None:
+            with torch.cuda.stream(h["stream"]):
+                ridx = torch.from_numpy(rows.astype(np.int32)).to(self.device, non_blocking=True)
         if n_warm:
-            s.load_state(self.store, idx, n_warm, stream=h["stream"])
+            # rows saved by batches on other handles: their saves come first
+            for w in np.unique(self.last_writer[rows[:n_warm]]):
+                if w >= 0 and w != me and self.handles[w]["save_event"] is not None:
+                    h["stream"].wait_event(self.handles[w]["save_event"])
+            s.load_state(self.store, ridx, n_warm, stream=h["stream"])
             self.warm_loads += n_warm
         s.solve(B, stream=h["stream"])
         if self.warm_shift is not None:
-            s.save_state(self.store, idx, B, shift=self.warm_shift, stream=h["stream"])
+            # one writer per row: an environment with several requests in the
+            # batch saves from its last slot only
+            save = np.full(B, -1, np.int32)
+            _, last = np.unique(envs[::-1], return_index=True)
+            keep = B - 1 - last
+            save[keep] = rows[keep]
+            with torch.cuda.stream(h["stream"]):
+                sidx = torch.from_numpy(save).to(self.device, non_blocking=True)
+            s.save_state(self.store, sidx, B, shift=self.warm_shift, stream=h["stream"])
+            ev_save = torch.cuda.Event()
+            ev_save.record(h["stream"])
+            h["save_event"] = ev_save
             self.has_state[envs] = True
-            h["idx_keep"] = idx
+            self.last_writer[rows] = me
+            h["idx_keep"] = (idx64, ridx, sidx)
+        h["rows"] = rows
         o = h["outs"]
         if self.early:
             # after each round: that round's statuses into pinned memory on the side stream
@@ -212,6 +363,9 @@ class BatchServer:
             o = {k: h["outs"][k][:hi - lo].cpu().numpy() for k in ("u", "xi", "kkt")}
             for i in range(hi - lo):
                 self.results[lo + int(order[i])] = {k: o[k][i] for k in o}
+        if h.get("rows") is not None:
+            self.rows.release(h["rows"])
+            h["rows"] = None
         h["busy"], h["event"], h["perm"] = None, None, None
 
     def step(self):

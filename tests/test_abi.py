@@ -103,3 +103,25 @@ def test_no_device_is_an_error_not_a_fallback(P):
     with pytest.raises(P.MpcError) as ei:
         P.Solver(P.default_config(13, 8, 3, 16, 20))
     assert ei.value.code == P.MPC_ERR_CUDA
+
+
+def test_workspace_and_state_estimates_on_the_host(P):
+    """mpc_workspace_estimate / mpc_state_floats_estimate size a handle for a
+    memory budget without a device: linear in B_max, errors for unbuilt
+    shapes (the GPU tests check the estimate equals mpc_workspace_bytes)."""
+    w1 = P.workspace_estimate(P.default_config(13, 8, 3, 100, 20))
+    w2 = P.workspace_estimate(P.default_config(13, 8, 3, 200, 20))
+    w3 = P.workspace_estimate(P.default_config(13, 8, 3, 300, 20))
+    assert 0 < w1 < w2 < w3 and (w3 - w2) == (w2 - w1)
+    # per instance at N = 20: records (47 KB), factor cache (33 KB), ADMM state (32 KB), gains (25 KB), outputs
+    assert 130_000 < (w2 - w1) / 100 < 160_000
+    lib = P.load()
+    out = ctypes.c_uint64()
+    assert lib.mpc_workspace_estimate(ctypes.byref(P.default_config(12, 8, 3, 16, 20)), ctypes.byref(out)) == \
+        P.MPC_ERR_UNSUPPORTED
+    assert lib.mpc_workspace_estimate(ctypes.byref(P.default_config(13, 8, 3, 0, 20)), ctypes.byref(out)) == \
+        P.MPC_ERR_INVALID_ARG
+    assert lib.mpc_workspace_estimate(None, ctypes.byref(out)) == P.MPC_ERR_INVALID_ARG
+    cfg = P.default_config(13, 8, 3, 16, 20)
+    assert P.state_floats_estimate(cfg, 20) == 2 * 5 * 20 * 40 + 8
+    assert P.state_floats_estimate(cfg, 0) == 0 and P.state_floats_estimate(cfg, 65) == 0

@@ -70,3 +70,30 @@ def test_warm_start_argument_checks(pinmpc):
     with pytest.raises(pinmpc.MpcError) as ei:
         s.warm_start(20)
     assert ei.value.code == pinmpc.MPC_ERR_INVALID_ARG
+
+
+def test_state_calls_reject_host_buffers(pinmpc):
+    """mpc_save_state / mpc_load_state check that the store and the row indices
+    are device memory of the handle's device before launching anything: a
+    host index array (natural from C or numpy) is an argument error, not a
+    kernel reading a host address."""
+    import torch
+    batch = W.generate(W.rl_scale_walking(B=8, N=10, seed=3))
+    s = pinmpc.solver_for(batch)
+    pinmpc.solve_workload(batch, solver=s)
+    F = s.state_floats(10)
+    store = torch.zeros((8, F), device="cuda")
+    host_idx = np.arange(8, dtype=np.int32)
+    host_store = np.zeros((8, F), np.float32)
+    for call in (lambda: s.save_state(store, host_idx, 8, shift=0),
+                 lambda: s.save_state(host_store, None, 8, shift=0),
+                 lambda: s.load_state(store, host_idx, 8),
+                 lambda: s.load_state(host_store, None, 8)):
+        with pytest.raises(pinmpc.MpcError) as ei:
+            call()
+        assert ei.value.code == pinmpc.MPC_ERR_INVALID_ARG
+    # device buffers still work afterwards
+    s.save_state(store, torch.arange(8, dtype=torch.int32, device="cuda"), 8, shift=0)
+    s.load_state(store, None, 8)
+    torch.cuda.synchronize()
+    s.close()

@@ -124,3 +124,32 @@ def test_served_warm_state_and_resets(pinmpc):
         want = cold if e in (3, 7) else warm
         assert srv.status[r] == 0 and np.array_equal(srv.results[r]["u"], want["u"][e]), e
     srv.close()
+
+
+@pytest.mark.gpu
+def test_back_to_back_requests_follow_serial_order(pinmpc):
+    # requests of one environment that land on different handles while the
+    # previous one is still on the GPU: each starts from the state its
+    # predecessor saved, exactly as a single handle's warm starts in series
+    from paper_2606_05687_b300.serve import BatchServer
+    batch = W.generate(W.rl_scale_walking(B=12, N=20, seed=25))
+    s = pinmpc.solver_for(batch)
+    serial = [pinmpc.solve_workload(batch, solver=s)]
+    for _ in range(3):
+        s.warm_start(0)
+        serial.append(pinmpc.solve_workload(batch, solver=s))
+    s.close()
+    for rep in range(2):
+        srv = BatchServer(pinmpc.device_inputs(batch), batch.nx, batch.nc, batch.contact_dim, B_max=1, N=batch.N,
+                          n_handles=3, warm_shift=0)
+        srv.keep_results = True
+        order = [5, 5, 5, 5, 9, 2, 9]
+        srv.submit(order)          # all queued at once: consecutive requests go to different handles
+        srv.drain()
+        seen = {}
+        for r, e in enumerate(order):
+            k = seen.get(e, 0)
+            seen[e] = k + 1
+            assert srv.status[r] == 0
+            assert np.array_equal(srv.results[r]["u"], serial[k]["u"][e]), (rep, r, e, k)
+        srv.close()
