@@ -85,25 +85,36 @@ def kernel_flops(iters, polishes, pivots, horizon, nx=13, nu=24):
             + 50 nbar (8.9 k at nx 13, nu 24), times stages x iterations.
     factor: per stage S_j (B B' and a 13x13 inversion, 2 n^3) and, after the
             first stage, W_j (T D^-1 T' and its inversion).
-    polish: per Riccati scan stage, the full-size stage products as
-            implemented -- S [Bt | A | et], [M | RHS] = Bt'[S Bt | -S A | s - S et],
-            G = S A + S Bt K, A'[G | g2] -- the rollout and the certificate's
-            costate and gradient products; per free pivot actually eliminated,
-            one Gauss-Jordan update of the nu x (nu + nx + 1) system."""
+    polish: the method's work of each Riccati scan stage on its free inputs
+            only (f of them: the inputs the stage's faces leave free), with f
+            the instance's mean over its scanned stages (pivots / (scans x
+            stages); using the mean undercounts the quadratic terms, so the
+            figure is a lower bound): S [Bt | A | et] (2 nx^2 (f + nx + 1)),
+            [M | RHS] = Bt'[...] (2 f nx (f + nx + 1)), G = S A + S Bt K
+            (2 nx f (nx + 1)), P = A'[G | g2] (2 nx^2 (nx + 1)), the rollout and
+            the certificate's costate and gradient products, and per free
+            pivot one Gauss-Jordan update of the f x (f + nx + 1) system.
+            ``polish_full`` counts the full-size products the kernel executes
+            (eliminated columns are unit vectors it still multiplies)."""
     nb, nk = nx + nu, nx + 1
     f_it = 2 * nu * nb + 2 * nb * nb + 4 * (nx * nx + nx * nu) + 2 * nx * nu + 50 * nb
     f_fac_s = 2 * nx * nx * nu + 2 * nx ** 3
     f_fac_w = 2 * nx * nx * nb + 2 * nx ** 3
-    f_stage = (2 * nx * nx * (nu + nx + 1) + 2 * nu * nx * (nu + nk) + 2 * nx * nu * nk + 2 * nx * nx * nk
-               + 2 * (nu * nk + nx * nx + nx * nu))
-    f_cert = 2 * nx * nx + 2 * nx * nu
-    f_piv = 2 * nu * (nu + nk)
     h = np.asarray(horizon, dtype=np.float64)
+    pol = np.asarray(polishes, np.float64)
+    piv = np.asarray(pivots, np.float64)
+
+    def stage_flops(f):
+        return (2 * nx * nx * (f + nx + 1) + 2 * f * nx * (f + nk) + 2 * nx * f * nk + 2 * nx * nx * nk
+                + 2 * (f * nk + nx * nx + nx * f) + 2 * nx * nx + 2 * nx * f)
+
+    scans = pol * h
+    f_mean = np.where(scans > 0, piv / np.maximum(scans, 1.0), 0.0)
     return {
         "factor": float(np.sum(h * f_fac_s + np.maximum(h - 1, 0) * f_fac_w)),
         "round": float(np.sum(np.asarray(iters, np.float64) * h) * f_it),
-        "polish": float(np.sum(np.asarray(polishes, np.float64) * h) * (f_stage + f_cert)
-                        + np.sum(np.asarray(pivots, np.float64)) * f_piv),
+        "polish": float(np.sum(scans * stage_flops(f_mean) + piv * 2 * f_mean * (f_mean + nk))),
+        "polish_full": float(np.sum(scans) * stage_flops(nu) + np.sum(piv) * 2 * nu * (nu + nk)),
     }
 
 
@@ -242,6 +253,11 @@ def oracle_sample(seconds: float, workers: int, start: int = 0):
     return done, elapsed, workers, refs
 
 
+def mi_over(args) -> dict:
+    """The iteration cap override of --max-iter (none: each shape's library default)."""
+    return {} if args.max_iter is None else {"max_iter": args.max_iter}
+
+
 def host_cores() -> int:
     return len(os.sched_getaffinity(0))
 
@@ -278,6 +294,77 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+def receding_leg(args, parts, MixedSolver, pinmpc, W, torch, steps=6, timed_from=2, sample=4):
+    """Configuration 3 as specified: a receding-horizon MPC loop over the
+    uneven batch.  Each step's stage data are the previous step's moved one
+    stage (the last repeated), its initial state the predicted xi_1 and its
+    previous input u_0 of each environment's last solution; the solve starts
+    from that solution's iterate moved one stage (mpc_warm_start) and is
+    replayed from a captured CUDA graph (one per shape).  The data shift
+    between steps runs on the device outside the timed region; each timed
+    step is set_stages + solve + get_traj of both shapes, concurrent on their
+    streams, timed with CUDA events.  Steps before `timed_from` capture the
+    graphs.  Oracle error: `sample` instances per shape of the last step."""
+    from oracle import qp as oqp
+    ms = MixedSolver(parts, graph=True, **mi_over(args))
+    ins = [pinmpc.device_inputs(p_, "cuda") for p_ in parts]
+
+    def shifted(t_, r_):
+        nt = {k: (v if k in ("xi0", "u_prev", "horizon") else torch.cat([v[:, 1:], v[:, -1:]], 1).contiguous())
+              for k, v in t_.items()}
+        nt["xi0"] = r_["xi"][:, 0].contiguous()
+        nt["u_prev"] = r_["u"][:, 0].contiguous()
+        return nt
+
+    ms.set_stages(ins)
+    ms.solve()
+    res = ms.results(device=True)
+    cur = torch.cuda.current_stream()
+    ms_step, cert, iters_, pol = [], [], [], []
+    for stp in range(steps):
+        ins = [shifted(t_, r_) for t_, r_ in zip(ins, res)]
+        torch.cuda.synchronize()
+        ms.warm_start(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for st_ in ms.streams:
+            st_.wait_stream(cur)
+        ms.set_stages(ins)
+        ms.solve(wait=False)
+        res = ms.results(device=True)
+        for st_ in ms.streams:
+            cur.wait_stream(st_)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        if stp >= timed_from:
+            ms_step.append(e0.elapsed_time(e1))
+            cert.append(int(sum(int((r_["status"] == 0).sum()) for r_ in res)))
+            iters_.append([float(r_["iters"].float().mean()) for r_ in res])
+    captures = [s_.graph_stats() for s_ in ms.solvers]
+    # oracle error of sampled instances of the last step
+    errs = []
+    for pi_, (p_, t_, r_) in enumerate(zip(parts, ins, res)):
+        ids = np.linspace(0, p_.B - 1, sample).astype(int)
+        sub = W.Batch(spec=p_.spec, nu_arr=p_.nu_arr[ids],
+                      **{k: (v[ids].cpu().numpy().view(np.uint32) if k == "mask" else v[ids].cpu().numpy())
+                         for k, v in t_.items()})
+        u_g = r_["u"][ids].cpu().numpy().astype(np.float64)
+        for i_ in range(len(ids)):
+            sol = oqp.solve_instance(oqp.instance(sub, i_))
+            nh = int(sub.horizon[i_])
+            errs.append(float(np.abs(u_g[i_, :nh] - sol.u).max() / max(np.abs(sol.u).max(), 1e-9)))
+    ms.close()
+    mean_ms = statistics.mean(ms_step)
+    total = sum(p_.B for p_ in parts)
+    return {"value": statistics.mean(cert) / (mean_ms / 1e3), "unit": "solves/s", "ms_per_step": mean_ms,
+            "certified_per_step": cert, "instances": total, "iters_mean_per_step": iters_,
+            "graph_captures_replays": captures,
+            "oracle_error": {"instances": len(errs), "u_rel_max": max(errs)},
+            "what": "receding-horizon steps of the uneven batch: data moved one stage, xi_0 / u_prev from the last "
+                    "solution, warm start moved one stage, solves replayed from CUDA graphs; "
+                    f"{steps - timed_from} timed steps after {timed_from} capture steps"}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -304,7 +391,7 @@ def run_gpu(args):
     # INFLIGHT batches on as many handles and streams: batch k+1's packing,
     # factors and first round overlap batch k's last rounds, which keep only
     # a few instances busy (the way a batched-solve service runs)
-    solvers = [pinmpc.solver_for(batch, max_iter=args.max_iter) for _ in range(INFLIGHT)]
+    solvers = [pinmpc.solver_for(batch, **mi_over(args)) for _ in range(INFLIGHT)]
     solver = solvers[0]
     streams = [torch.cuda.current_stream(dev)] + [torch.cuda.Stream(dev) for _ in range(INFLIGHT - 1)]
     stream = streams[0]
@@ -453,7 +540,7 @@ def run_gpu(args):
         # when the round that certifies its instance ends
         from paper_2606_05687_b300.serve import BatchServer, poisson_arrivals, serve_load
         srv = BatchServer(t, batch.nx, batch.nc, batch.contact_dim, B_max=B, N=N, n_handles=SERVE_HANDLES,
-                          max_iter=args.max_iter)
+                          **mi_over(args))
         serve_load(srv, poisson_arrivals(0.7 * value, 0.2, B, seed=SEED + 1))  # warm-up
         served = serve_load(srv, poisson_arrivals(0.7 * value, 1.0, B, seed=SEED))
         srv.close()
@@ -508,7 +595,7 @@ def run_gpu(args):
                 big.solve(B, stream=s0)
                 host_us.append((time.perf_counter() - h0) * 1e6)
             s0.synchronize()
-            small = pinmpc.solver_for(sub, max_iter=args.max_iter)
+            small = pinmpc.solver_for(sub, **mi_over(args))
             small.set_graph_mode(mode == "graph")
             xo = torch.empty((64, N, 13), device=dev)
             uo = torch.empty((64, N, 24), device=dev)
@@ -549,7 +636,7 @@ def run_gpu(args):
         pool["horizon"] = torch.from_numpy(rng_h.choice(np.array([10, 20, 30], np.int32), size=n_env)).to("cuda")
         del ft
         fsrv = BatchServer(pool, fb.nx, fb.nc, fb.contact_dim, B_max=8192, N=nf, n_handles=SERVE_HANDLES,
-                           warm_shift=1, horizon_classes=pinmpc.horizon_classes_for(nf), max_iter=args.max_iter)
+                           warm_shift=1, horizon_classes=pinmpc.horizon_classes_for(nf), **mi_over(args))
         fleet = fleet_load(fsrv, hz=50.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 3)
         # below capacity: the same fleet ticking at 10 Hz (655k requests/s offered)
         fleet["at_10hz"] = fleet_load(fsrv, hz=10.0, duration=2.0, warmup=0.5, reset_rate=0.5, seed=SEED + 4)
@@ -577,7 +664,7 @@ def run_gpu(args):
         # contact model, both solved concurrently on their streams
         from paper_2606_05687_b300.mixed import MixedSolver
         parts = [W.generate(sp) for sp in W.uneven_mixed(B=16384, N=40, seed=SEED + 1)]
-        ms = MixedSolver(parts, max_iter=args.max_iter)
+        ms = MixedSolver(parts, **mi_over(args))
         ms.set_stages([pinmpc.device_inputs(p_, "cuda") for p_ in parts])
         ms.solve()
         torch.cuda.synchronize()
@@ -591,12 +678,16 @@ def run_gpu(args):
         res_ = ms.results()
         ms.close()
         ok_ = int(sum((r_["status"] == 0).sum() for r_ in res_))
+        uncert = [{"part": pi_, "instance": int(b_), "status": int(r_["status"][b_]), "iters": int(r_["iters"][b_]),
+                   "kkt": float(r_["kkt"][b_])}
+                  for pi_, r_ in enumerate(res_) for b_ in np.flatnonzero(r_["status"] != 0)]
         uneven = {"value": ok_ / umt, "unit": "solves/s", "instances": 16384, "certified": ok_,
-                  "ms_per_solve": umt * 1e3,
+                  "ms_per_solve": umt * 1e3, "uncertified": uncert[:8],
                   "iters_mean": [float(r_["iters"].mean()) for r_ in res_],
                   "workload": "16384 envs: 8192 walking (8 point contacts) + 8192 Bernoulli-stance (2 foot wrenches), "
                               "horizons U{5..40}, stage stride 40, horizon classes (10, 20, 32, 40), both shapes solved concurrently "
-                              "(inputs resident)"}
+                              "(inputs resident), cold start"}
+        uneven["receding"] = receding_leg(args, parts, MixedSolver, pinmpc, W, torch)
 
     plain = None
     if not args.device_only:
@@ -650,6 +741,55 @@ def run_gpu(args):
                                      "u_rel_max": float(np.max(e_p))}
         pa.close()
 
+    precision = None
+    if not args.device_only:
+        # reduced-precision caches (mpc_config.precision): the Gram products of
+        # the factor kernel on the tensor cores in TF32 / BF16 (FP32
+        # accumulation), the rest FP32; same batch, one batch in flight,
+        # every launch timed by the library's events; per-instance error
+        # against the oracle beside the FP32 path's (oracle_error)
+        precision = {}
+        for pname, pval in (("tf32", pinmpc.PREC_TF32), ("bf16", pinmpc.PREC_BF16)):
+            ps = pinmpc.solver_for(batch, **mi_over(args), precision=pval)
+            pout = device_outputs()
+            s0 = streams[0]
+
+            def prec_step():
+                ps.set_stages(B, N, **t, stream=s0)
+                ps.solve(B, stream=s0)
+                ps.get_traj(pout["xi"], pout["u"], pout["st"], pout["it"], pout["kk"], None, stream=s0)
+
+            prec_step()
+            barrier()
+            ps.set_kernel_timing(True)
+            reps = 3
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s0)
+            for _ in range(reps):
+                prec_step()
+            e1.record(s0)
+            barrier()
+            q_ms = e0.elapsed_time(e1) / reps
+            qk = ps.kernel_times(reset=True)
+            ps.set_kernel_timing(False)
+            q_st, q_it, q_kk = pout["st"].cpu().numpy(), pout["it"].cpu().numpy(), pout["kk"].cpu().numpy()
+            q_ok = int(((q_st == 0) & (q_kk <= KKT_TOL)).sum())
+            entry = {"solves_per_s": q_ok / (q_ms / 1e3), "ms_per_solve": q_ms, "certified": q_ok,
+                     "kkt_max": float(q_kk.max()), "iters_mean": float(q_it.mean()),
+                     "factor_ms_per_launch": qk["factor"][0] / max(qk["factor"][1], 1)}
+            if refs:
+                u_q = pout["u"].cpu().numpy().astype(np.float64)
+                e_q = [np.abs(u_q[b_, :int(batch.horizon[b_])] - u_r).max() / max(np.abs(u_r).max(), 1e-9)
+                       for b_, (_, u_r) in refs.items()]
+                entry["oracle_error"] = {"instances": len(e_q), "u_rel_max": float(np.max(e_q)),
+                                         "u_rel_p99": float(np.percentile(e_q, 99))}
+            precision[pname] = entry
+            ps.close()
+        precision["fp32_factor_ms_per_launch"] = ktimes["factor"][0] / max(ktimes["factor"][1], 1)
+        precision["what"] = ("Gram products B B' and T D'^-1 T' of the factor kernel (the caches behind J_k, H_k) "
+                             "on the tensor cores (mma.sync, FP32 accumulation); one batch in flight, 3 solves; "
+                             "solves_per_s counts certified solves (KKT <= 1e-5)")
+
     if rank != 0:
         return
     # roofline of the dominant kernel from the live per-kernel times (each
@@ -662,6 +802,9 @@ def run_gpu(args):
             continue
         tfl = fl.get(name, 0.0) * args.steps / (ms / 1e3) / 1e12 if name in fl else None
         kernels[name] = {"launches": n, "ms_per_launch": ms / n, "share": ms / kt_total, "achieved_tflops": tfl}
+        if name == "polish":
+            # the full-size products the kernel executes, beside the method's work
+            kernels[name]["executed_tflops"] = fl["polish_full"] * args.steps / (ms / 1e3) / 1e12
     dom = max((k for k in kernels if k in fl), key=lambda k: ktimes[k][0])
     achieved = kernels[dom]["achieved_tflops"]
     solve_avg = statistics.mean(solve_ms)
@@ -689,7 +832,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "global_batch": world * B, "horizon": N, "seed": SEED,
                    "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
                    "inflight": INFLIGHT,
-                   "max_iter": args.max_iter},
+                   "max_iter": args.max_iter or "library default per shape"},
         "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
                 if e2e_val is not None else None),
         "single_stream": single,
@@ -699,6 +842,7 @@ def run_gpu(args):
         "uneven": uneven,
         "fleet": fleet,
         "plain_admm": plain,
+        "precision": precision,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
@@ -747,7 +891,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--max-iter", type=int, default=1000)
+    ap.add_argument("--max-iter", type=int, default=None,
+                    help="ADMM iteration cap of every leg (default: the library's per-shape default)")
     ap.add_argument("--inflight", type=int, default=INFLIGHT, help="batches in flight (handles and streams)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

@@ -4,9 +4,11 @@
  * Each instance b of a batch is the linear time-varying MPC problem of
  * Sec. III (the standard form stated there, with C = I):
  *
- *   min  sum_{k=0}^{N-1} 1/2 ||xi_{k+1} - r^y_k||^2_{Q_k} + 1/2 ||u_k - r^u_k||^2_{R_k}
+ *   min  sum_{k=0}^{N-1} 1/2 ||C_k xi_{k+1} - r^y_k||^2_{Q_k} + 1/2 ||u_k - r^u_k||^2_{R_k}
  *   s.t. xi_{k+1} = A_k xi_k + B_k u_k + e_k,   xi_0 given,
- *        u_k in U_k  (a product over contacts of contact sets).
+ *        xi_{k+1} in X_k (an optional box),
+ *        u_k in U_k  (a product over contacts of contact sets),
+ * with C_k diagonal (I unless given).
  *
  * Contact sets (Sec. II-B names the friction pyramid and the contact wrench
  * cone): a stance contact's components (t, n) lie in the generalized pyramid
@@ -28,7 +30,8 @@
  * Conventions
  *   - All functions return an mpc_status; none aborts or traps.
  *   - Floating-point data is FP32, row-major, instance-major: stage arrays are
- *     [B][N][...] with the stage stride N = the view's N (<= N_max).
+ *     [B][S][...] with S = the view's stage_stride (default its N <= N_max),
+ *     of which the first N stages of each instance are read.
  *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
  *     void*; NULL = the legacy default stream) and is asynchronous unless
  *     stated otherwise.
@@ -63,6 +66,7 @@ enum {
     MPC_BAD_SET = 3,    /* empty contact set (n_max < 0 or mu < 0 on a stance contact) */
     MPC_TIMEOUT = 4,    /* reserved for bounded device-side waits */
     MPC_BAD_HORIZON = 5, /* horizon[b] outside [1, N] */
+    MPC_BAD_DIM = 6,     /* nu[b] not a multiple of contact_dim in [0, nu] */
     MPC_RUNNING = -1     /* not finished yet: read before the solve has passed
                             the round that finishes the instance */
 };
@@ -103,6 +107,12 @@ typedef struct mpc_config {
                               iteration, the polish and the certificate stay FP32: the
                               certified KKT bound holds for every mode (the polish and its
                               refinement recover what the rounded caches lose) */
+    float kkt_tol_abs;     /* absolute part of the certificate's tolerance: each KKT term must
+                              satisfy |residual| <= kkt_tol_abs + kkt_tol * scale, its scale
+                              being n_max (feasibility), max(|R(u - r^u)|, |B'y|)
+                              (stationarity) or |u|_inf (complementarity); the reported kkt is
+                              max |residual| / (kkt_tol_abs / kkt_tol + scale).  0 = kkt_tol
+                              (the default: |residual| / (1 + scale) <= kkt_tol) */
 } mpc_config;
 
 /* mpc_config.precision */
@@ -125,6 +135,26 @@ typedef struct mpc_stage_view {
     const float* xi0;       /* [B][nx]         initial state, required */
     const float* u_prev;    /* [B][nu]         u_{-1} of the velocity form, NULL = 0 */
     const int32_t* horizon; /* [B]            per-instance horizon <= N, NULL = N */
+    const float* C;         /* [B][N][nx]     diagonal of the output map C_k of the stage cost
+                                              1/2 ||C_k xi_{k+1} - r^y_k||^2_{Q_k} (Sec. III's standard
+                                              form); NULL = I.  Diagonal maps only (a weight or a
+                                              selection per state component); a zero entry drops that
+                                              component from the cost */
+    const int32_t* nu;      /* [B]            inputs present in instance b: a multiple of contact_dim
+                                              up to the handle's nu; its first nu[b] / contact_dim
+                                              contacts take part, the others are absent (held at 0,
+                                              whatever their mask bits).  NULL = all.  Another count
+                                              gives that instance the status MPC_BAD_DIM */
+    int32_t stage_stride;   /* stages between consecutive instances in the stage arrays, >= N (the
+                               arrays are [B][stage_stride][...] and the first N stages of each
+                               instance are read); 0 = N */
+    const float* xlo;       /* [B][N][nx]     state box X_k of Sec. III's standard form,       */
+    const float* xhi;       /* [B][N][nx]     xlo_k <= xi_{k+1} <= xhi_k (+-INFINITY: unbounded
+                                              component); either or both NULL = unbounded.  The
+                                              ADMM projects the state part of z onto the box; the
+                                              polish holds the bounds its iterate sits at by an
+                                              augmented Lagrangian, and the certificate includes
+                                              their feasibility and multipliers */
 } mpc_stage_view;
 
 typedef struct mpc_handle mpc_handle;

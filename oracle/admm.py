@@ -107,9 +107,14 @@ def lift(inst, u_prev=None, xlo=None, xhi=None, dx=proj.FOOT_HALF_LENGTH,
         Bbar[k, :nx] = inst.Bm[k]
         Bbar[k, nx:] = np.eye(nu)
         ebar[k, :nx] = inst.e[k]
-    Qbar = np.concatenate([inst.Q, inst.R], axis=1)
-    qbar = np.concatenate([inst.Q * inst.ry, inst.R * inst.ru], axis=1)
+    cd = np.ones_like(inst.Q) if getattr(inst, "C", None) is None else inst.C
+    # cost 1/2 ||C xi - r^y||^2_Q on the state part: C'QC and C'Q r^y (C diagonal)
+    Qbar = np.concatenate([cd * inst.Q * cd, inst.R], axis=1)
+    qbar = np.concatenate([cd * inst.Q * inst.ry, inst.R * inst.ru], axis=1)
     up = np.zeros(nu) if u_prev is None else np.asarray(u_prev, dtype=np.float64)
+    if xlo is None and xhi is None and (getattr(inst, "xlo", None) is not None or getattr(inst, "xhi", None) is not None):
+        xlo = inst.xlo if inst.xlo is not None else np.full((N, nx), -np.inf)
+        xhi = inst.xhi if inst.xhi is not None else np.full((N, nx), np.inf)
     return Lifted(Abar=Abar, Bbar=Bbar, ebar=ebar, Qbar=Qbar, qbar=qbar,
                   xibar0=np.concatenate([inst.xi0, up]), stance=np.asarray(inst.stance, bool),
                   mu=inst.mu, fmax=inst.fmax, contact_dim=inst.contact_dim, nx=nx,

@@ -10,7 +10,8 @@ Problem (Sec. III, the LTV-MPC standard form, C = I):
 
 The states are eliminated (condensing): X = Gamma U + X_free, giving a dense
 strictly convex QP in the stance inputs only, min 1/2 U'HU + c'U s.t. GU <= h,
-solved by Mehrotra's predictor-corrector primal-dual interior-point method
+(state boxes lo_k <= xi_{k+1} <= hi_k, where given, are rows of G on
+Gamma U), solved by Mehrotra's predictor-corrector primal-dual interior-point method
 (Nocedal & Wright, Numerical Optimization, 2nd ed., Alg. 16.4).  numpy's
 dense solve serves as the linear-algebra step.
 """
@@ -44,6 +45,12 @@ class Instance:
     stance: np.ndarray  # bool [N,nc]
     xi0: np.ndarray    # [nx]
     contact_dim: int
+    C: Optional[np.ndarray] = None  # [N,nx] diagonal output map of the cost ||C xi - r^y||_Q (None = I)
+    xlo: Optional[np.ndarray] = None  # [N,nx] state box lo_k <= xi_{k+1} (None / -inf = unbounded)
+    xhi: Optional[np.ndarray] = None  # [N,nx] state box xi_{k+1} <= hi_k (None / +inf = unbounded)
+
+    def cdiag(self) -> np.ndarray:
+        return np.ones_like(self.Q) if self.C is None else self.C
 
     @property
     def N(self):
@@ -101,9 +108,11 @@ def assemble(inst: Instance):
     N, nx, nu, cd = inst.N, inst.nx, inst.nu, inst.contact_dim
     Gamma, Xf = condense(inst)
     Qd = inst.Q.reshape(-1)
+    Cd = inst.cdiag().reshape(-1)
     Rd = inst.R.reshape(-1)
-    H = Gamma.T @ (Qd[:, None] * Gamma) + np.diag(Rd)
-    c = Gamma.T @ (Qd * (Xf - inst.ry.reshape(-1))) - Rd * inst.ru.reshape(-1)
+    # 1/2 ||C X - r||^2_Q = 1/2 X'(C Q C)X - (C Q r)'X + const, X = Gamma U + Xf
+    H = Gamma.T @ ((Cd * Qd * Cd)[:, None] * Gamma) + np.diag(Rd)
+    c = Gamma.T @ (Cd * Qd * (Cd * Xf - inst.ry.reshape(-1))) - Rd * inst.ru.reshape(-1)
     keep = np.zeros(N * nu, dtype=bool)
     for k in range(N):
         for i in range(inst.nc):
@@ -124,6 +133,15 @@ def assemble(inst: Instance):
                 Grows.append(row)
                 hrows.append(hi[r])
     nk = int(keep.sum())
+    # state boxes X_k on xi_{k+1} = (Gamma U + Xf) rows: finite bounds become rows
+    Gk = Gamma[:, keep]
+    for lim, sgn in ((inst.xhi, 1.0), (inst.xlo, -1.0)):
+        if lim is None:
+            continue
+        flat = np.asarray(lim, dtype=np.float64).reshape(-1)
+        for idx in np.flatnonzero(np.isfinite(flat)):
+            Grows.append(sgn * Gk[idx])
+            hrows.append(sgn * (flat[idx] - Xf[idx]))
     G = np.array(Grows).reshape(len(Grows), nk)
     h = np.array(hrows)
     return H[np.ix_(keep, keep)], c[keep], G, h, keep
@@ -203,7 +221,7 @@ class Solution:
 
 
 def objective(inst: Instance, xi: np.ndarray, u: np.ndarray) -> float:
-    dx = xi - inst.ry
+    dx = inst.cdiag() * xi - inst.ry
     du = u - inst.ru
     return 0.5 * float(np.sum(inst.Q * dx * dx) + np.sum(inst.R * du * du))
 

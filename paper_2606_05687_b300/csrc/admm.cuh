@@ -181,6 +181,7 @@ struct StageRegs {
     float ir1, ir2;           // contact lane q: 1/(1 + mu^2), 1/(1 + 2 mu^2) (point contacts)
     uint32_t stance;          // contact lane q is in stance
     uint32_t mw;              // contact lane q: faces of the latest projection
+    float xlo, xhi;           // state lane i < NX: box of component i of xi_{j+1} (+-inf: none)
     float ax[2];              // Abar_j xibar_j
     float bd[2];              // B_j du_j (state rows) and du_j (input rows)
     float zh[2], vh[2], thh[2], beh[2], lah[2];  // extrapolated iterate of stage j
@@ -317,7 +318,7 @@ __device__ __forceinline__ void block1_r(const RCtx<D>& c, const RegT<D>& M, Sta
 
 // Block 2 and the dual ascents of stage j; new values go to buffer 1 - cb.
 // Returns the stage's share of the combined residual (valid in every lane).
-template <class D, bool CL = false>
+template <class D, bool CL = false, bool BOX = false>
 __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int cb, int j, int lane, float dx,
                                           float dy) {
     constexpr int NX = D::NX, NB = D::NB, NBP = D::NBP, CD = D::CD;
@@ -357,7 +358,8 @@ __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int
     float* nxt = c.var + RoundState<D>::at(c.N, 1 - cb, j, 0);
     float cm = 0.0f;
     if (v0) {
-        const float z = lane < NX ? a0 : zp[lane];
+        // z = Proj onto X_j x U_j: the state part clipped to its box (when set)
+        const float z = lane < NX ? (BOX ? fminf(fmaxf(a0, R.xlo), R.xhi) : a0) : zp[lane];
         const float v = 0.5f * (z + ga0);
         const float th = R.thh[0] + xn0 - z;
         const float be = R.beh[0] + R.bd[0] - v;
@@ -572,15 +574,17 @@ __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a)
     __syncwarp();
     bool bad = false, badset = false;
     for (int e = lane; e < D::oMASK; e += 32) bad |= !isfinite(sr[e]);
+    int packbits = 0;
     if (j == 0) {
         for (int i = lane; i < NB; i += 32)
             bad |= !isfinite(__ldg(tail + (i < NX ? D::tXI0 + i : D::tUP + i - NX)));
+        packbits = __float_as_int(__ldg(tail + D::tFLAG));  // 4: bad per-instance input count
     }
     const uint32_t mk = __float_as_uint(sr[D::oMASK]);
     if (lane < D::NC && ((mk >> lane) & 1u)) badset = sr[D::oMU + lane] < 0.0f || sr[D::oFM + lane] < 0.0f;
     bad = __any_sync(0xffffffffu, bad);
     badset = __any_sync(0xffffffffu, badset);
-    if (lane == 0 && (bad || badset)) atomicOr(a.flags + b, (bad ? 1 : 0) | (badset ? 2 : 0));
+    if (lane == 0 && (bad || badset || packbits)) atomicOr(a.flags + b, (bad ? 1 : 0) | (badset ? 2 : 0) | packbits);
     float* gc = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
     const int r = lane >> 1;
     float row[NX];
@@ -611,6 +615,30 @@ __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a)
     }
 }
 
+// State box of global stage jg (the bounds of xi_{jg+1}) into the state lanes' registers.
+template <class D>
+__device__ __forceinline__ void load_box(const RoundArgs& a, int b, int jg, int lane, StageRegs<D>& R) {
+    R.xlo = -INFINITY;
+    R.xhi = INFINITY;
+    if (a.xbox && lane < D::NX) {
+        const float* bx = a.xbox + ((size_t)b * a.n_rec + jg) * 2 * D::NX;
+        R.xlo = bx[lane];
+        R.xhi = bx[D::NX + lane];
+    }
+}
+
+// After a round, the state bounds z_{jg+1} sits at (its clip is exact, so
+// equality marks an active bound): bit i lower, bit 16 + i upper.  Whole warp.
+template <class D>
+__device__ __forceinline__ void store_box_bits(const RoundArgs& a, int b, int jg, int lane, const StageRegs<D>& R,
+                                               const float* zcur) {
+    if (!a.xbox) return;
+    const float z = lane < D::NX ? zcur[lane] : 0.0f;
+    const unsigned lo = __ballot_sync(0xffffffffu, lane < D::NX && z <= R.xlo);
+    const unsigned hi = __ballot_sync(0xffffffffu, lane < D::NX && z >= R.xhi);
+    if (lane == 0) a.smodes[(size_t)b * a.N + jg] = (lo & 0xffffu) | (hi << 16);
+}
+
 // Writes a failure status for instance b (no iterate): zero trajectory and inputs.
 template <class D>
 __device__ void round_fail(const RoundArgs& a, int b, int status) {
@@ -633,7 +661,7 @@ __device__ void round_fail(const RoundArgs& a, int b, int status) {
 // CTA's shared memory holds cap stages: N, or with CAPPED a.cap < N (the
 // launch serves a horizon class whose horizons all fit).  The uncapped form
 // is compiled with cap = N throughout.
-template <class D, int MAXT, bool CAPPED>
+template <class D, int MAXT, bool CAPPED, bool BOX>
 __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float* smem, int buf) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     constexpr bool TWO = RegT<D>::kTwo;
@@ -652,7 +680,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
     if (a.m0 == 0) {
         const int fl = a.flags[b];  // written by factor_kernel
         if (fl) {
-            round_fail<D>(a, b, (fl & 1) ? kNonFinite : kBadSet);
+            round_fail<D>(a, b, (fl & 1) ? kNonFinite : ((fl & 4) ? kBadDim : kBadSet));
             return;
         }
     }
@@ -713,6 +741,8 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
             }
         }
         for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
+        if constexpr (BOX)
+            for (int e = tid; e < a.N; e += nthr) a.slast[(size_t)b * a.N + e] = 0xffffffffu;
         if (tid == 0) {
             a.out_npol[b] = 0;
             a.out_piv[b] = 0;
@@ -762,6 +792,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         R.ir2 = 1.0f / (1.0f + 2.0f * R.mu * R.mu);
         R.stance = (mask(j) >> q) & 1u;
         R.mw = 0u;
+        if constexpr (BOX) load_box<D>(a, b, j, lane, R);
     }
     __syncthreads();
     // Abar_0 xibar_0 is constant; the other stages form theirs every iteration
@@ -791,7 +822,7 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         }
         __syncthreads();
         if (active) {
-            const float cm = block2_r<D>(c, R, cb, j, lane, a.dx, a.dy);
+            const float cm = block2_r<D, false, BOX>(c, R, cb, j, lane, a.dx, a.dy);
             if (lane == 0) c.part[j] = cm;
         }
         __syncthreads();
@@ -825,6 +856,8 @@ __device__ __forceinline__ void round_instance(const RoundArgs& a, int b, float*
         }
     }
     if (active && lane < D::NC && a.m1 > a.m0) a.modes[((size_t)b * a.N + j) * D::NC + lane] = R.mw;
+    if constexpr (BOX)
+        if (active && a.m1 > a.m0) store_box_bits<D>(a, b, j, lane, R, c.var + RoundState<D>::at(cap, cb, j, VZ));
     if (tid == 0) {
         float* sc = gstate + nvar;
         sc[RoundState<D>::sAlpha] = alpha;
@@ -890,7 +923,7 @@ __device__ __noinline__ void round_fetch(const RoundArgs& a, float* smem, uint64
 // With a.dbl, thread 0 starts the TMA copies of the next instance's records
 // and factors into the other buffer as soon as it knows that instance, so
 // they arrive while the current instance iterates.
-template <class D, int MAXT, bool CAPPED = false>
+template <class D, int MAXT, bool CAPPED = false, bool BOX = false>
 __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int item;
@@ -922,7 +955,7 @@ __global__ void __launch_bounds__(MAXT, 1) round2_kernel(RoundArgs a) {
                 return;
             }
         }
-        round_instance<D, MAXT, CAPPED>(a, b, smem, cur);
+        round_instance<D, MAXT, CAPPED, BOX>(a, b, smem, cur);
         if (bn < 0) break;
         b = bn;
     }

@@ -69,41 +69,53 @@ void launch_factor_t(const FactorArgs& a, cudaStream_t s) {
     else if (a.precision == kPrecBF16) factor_kernel<D, kPrecBF16><<<grid, 32 * kFactorWarps, 0, s>>>(a);
     else factor_kernel<D><<<grid, 32 * kFactorWarps, 0, s>>>(a);
 }
-template <class D>
-cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(round2_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+template <class D, bool BOX>
+cudaError_t set_round_attrs_b(int round_bytes, int polish_bytes) {
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(round2_kernel<D, 640, false, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(round2_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    e = cudaFuncSetAttribute(round2_kernel<D, 1024, false, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(round2_kernel<D, 640, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    e = cudaFuncSetAttribute(round2_kernel<D, 640, true, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(round2_kernel<D, 1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    e = cudaFuncSetAttribute(round2_kernel<D, 1024, true, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(round_cl_kernel<D, 640>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    e = cudaFuncSetAttribute(round_cl_kernel<D, 640, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(round_cl_kernel<D, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, round_bytes);
+    e = cudaFuncSetAttribute(round_cl_kernel<D, 1024, BOX>, attr, round_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(polish_cta_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, polish_bytes);
+    return cudaFuncSetAttribute(polish_cta_kernel<D, BOX>, attr, polish_bytes);
 }
 template <class D>
-void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
+cudaError_t set_round_attrs_t(int round_bytes, int polish_bytes) {
+    const cudaError_t e = set_round_attrs_b<D, false>(round_bytes, polish_bytes);
+    return e != cudaSuccess ? e : set_round_attrs_b<D, true>(round_bytes, polish_bytes);
+}
+// The round kernel's launch form (the state-box variant when boxes are set).
+template <class D, bool BOX>
+void launch_round_b(const RoundArgs& a, int B, int smem, cudaStream_t s) {
     // register-heavy form for up to 20 stages per CTA (640 threads), 64-register
     // form above; B persistent workers: CTAs, or CTA pairs above 32 stages.
     // The launch's stage capacity is a.cap (its horizon class's, N for one class).
     const int n = a.cap;
     if (n > 32) {
         const int nl = (n + 1) / 2;
-        if (nl <= 20) round_cl_kernel<D, 640><<<2 * B, 32 * nl, smem, s>>>(a);
-        else round_cl_kernel<D, 1024><<<2 * B, 32 * nl, smem, s>>>(a);
+        if (nl <= 20) round_cl_kernel<D, 640, BOX><<<2 * B, 32 * nl, smem, s>>>(a);
+        else round_cl_kernel<D, 1024, BOX><<<2 * B, 32 * nl, smem, s>>>(a);
     } else if (n < a.N) {
         // a horizon class below N: CTAs sized for n stages
-        if (n <= 20) round2_kernel<D, 640, true><<<B, 32 * n, smem, s>>>(a);
-        else round2_kernel<D, 1024, true><<<B, 32 * n, smem, s>>>(a);
+        if (n <= 20) round2_kernel<D, 640, true, BOX><<<B, 32 * n, smem, s>>>(a);
+        else round2_kernel<D, 1024, true, BOX><<<B, 32 * n, smem, s>>>(a);
     } else if (n <= 20) {
-        round2_kernel<D, 640><<<B, 32 * n, smem, s>>>(a);
+        round2_kernel<D, 640, false, BOX><<<B, 32 * n, smem, s>>>(a);
     } else {
-        round2_kernel<D, 1024><<<B, 32 * n, smem, s>>>(a);
+        round2_kernel<D, 1024, false, BOX><<<B, 32 * n, smem, s>>>(a);
     }
+}
+template <class D>
+void launch_round_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
+    if (a.xbox) launch_round_b<D, true>(a, B, smem, s);
+    else launch_round_b<D, false>(a, B, smem, s);
 }
 template <class D>
 void launch_bin_t(const RoundArgs& a, int B, cudaStream_t s) {
@@ -111,7 +123,8 @@ void launch_bin_t(const RoundArgs& a, int B, cudaStream_t s) {
 }
 template <class D>
 void launch_polish_t(const RoundArgs& a, int B, int smem, cudaStream_t s) {
-    polish_cta_kernel<D><<<B, kPT, smem, s>>>(a);
+    if (a.xbox) polish_cta_kernel<D, true><<<B, kPT, smem, s>>>(a);
+    else polish_cta_kernel<D><<<B, kPT, smem, s>>>(a);
 }
 template <class D>
 int resident_per_sm_t(int kernel, int N, int smem) {
@@ -199,6 +212,10 @@ struct mpc_handle {
     uint32_t* lastm = nullptr;   // [B_max][N_max][nc]
     int* done = nullptr;         // [B_max]
     int* flags = nullptr;        // [B_max] input-check bits of the factor kernel
+    float* xbox = nullptr;       // [B_max][N_max][2][nx] state boxes of the last set_stages
+    uint32_t* smodes = nullptr;  // [B_max][N_max] state bounds of the latest z
+    uint32_t* slast = nullptr;   // [B_max][N_max] state bounds of the last polish
+    bool box_set = false;        // the last set_stages gave state boxes
     int* lists = nullptr;        // [2][kMaxClasses][B_max] instances still running, by round parity and horizon class
     int* work = nullptr;         // [kMaxClasses] round cursors, then list counts [2][kMaxClasses]
     int ncls_req = 0;            // horizon classes below N (mpc_set_horizon_classes), ascending caps
@@ -232,6 +249,7 @@ struct mpc_handle {
     // (B, N, double buffering, warm-start count), most recent last
     struct SolveGraph {
         int B, N, dbl, warm_B;
+        bool box;
         cudaGraphExec_t exec;
     };
     bool graph_mode = false;
@@ -388,7 +406,8 @@ static uint64_t workspace_bytes_of(const mpc_config& c, const Shape& sh) {
     const size_t kst_b = B * N * nu * (c.nx + 1) * sizeof(float);
     const size_t round_b = cache_b + state_b + 2 * modes_b + (2 + 2 * kMaxClasses) * B * sizeof(int) +
                            3 * kMaxClasses * sizeof(int) + kst_b;
-    return rec_b + xi_b + u_b + small_b + round_b;
+    const size_t box_b = B * N * (2 * (size_t)c.nx * sizeof(float) + 2 * sizeof(uint32_t));
+    return rec_b + xi_b + u_b + small_b + round_b + box_b;
 }
 
 extern "C" {
@@ -430,6 +449,7 @@ mpc_status mpc_default_config(mpc_config* cfg, int32_t nx, int32_t n_contacts, i
     cfg->mem_budget = 0;
     cfg->device = 0;
     cfg->precision = MPC_PREC_FP32;
+    cfg->kkt_tol_abs = 0.0f;
     if (nx == 13 && contact_dim == 6) {
         // foot wrenches on the 13-state model: a stiffer penalty, a later
         // first check and finer, longer refinement (measured: 2.3-6x faster,
@@ -470,7 +490,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     if (!(c.rho > 0.0f) || !(c.u_scale > 0.0f) || !(c.kkt_tol > 0.0f) || c.max_iter < 1 ||
         c.check_every < 1 || c.check_start < 1 || !(c.check_growth >= 1.0f) || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) ||
         !(c.foot_half_length >= 0.0f) || !(c.foot_half_width >= 0.0f) || c.refine_steps < 0 ||
-        !(c.refine_alpha > 0.0f) || c.precision < MPC_PREC_FP32 || c.precision > MPC_PREC_BF16)
+        !(c.refine_alpha > 0.0f) || c.precision < MPC_PREC_FP32 || c.precision > MPC_PREC_BF16 ||
+        !(c.kkt_tol_abs >= 0.0f))
         return fail(nullptr, MPC_ERR_INVALID_ARG, "invalid solver parameter");
     if (c.N_max > kClusterMaxN)
         return fail(nullptr, MPC_ERR_UNSUPPORTED, "N_max=%d exceeds %d stages (one warp per stage, two CTAs)",
@@ -534,7 +555,10 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
               cudaMalloc(&h->done, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->flags, B * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&h->lists, 2 * kMaxClasses * B * sizeof(int)) == cudaSuccess &&
-              cudaMalloc(&h->work, 3 * kMaxClasses * sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess;
+              cudaMalloc(&h->work, 3 * kMaxClasses * sizeof(int)) == cudaSuccess && cudaMalloc(&h->Kst, kst_b) == cudaSuccess &&
+              cudaMalloc(&h->xbox, B * N * 2 * c.nx * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&h->smodes, B * N * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMalloc(&h->slast, B * N * sizeof(uint32_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         const unsigned long long want = h->bytes;
@@ -556,16 +580,23 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaSetDevice(c.device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (v->stage_stride != 0 && v->stage_stride < v->N)
+        return fail(h, MPC_ERR_INVALID_ARG, "stage_stride=%d below N=%d", v->stage_stride, v->N);
     const size_t B = v->B, N = v->N, nx = c.nx, nu = h->nu, nc = h->nc;
-    const void* src[13] = {v->A, v->Bm, v->e, v->Q, v->R, v->ry, v->ru, v->mu, v->fmax, v->xi0, v->u_prev, v->mask, v->horizon};
-    const size_t cnt[13] = {B * N * nx * nx, B * N * nx * nu, B * N * nx, B * N * nx, B * N * nu, B * N * nx,
-                            B * N * nu, B * N * nc, B * N * nc, B * nx, B * nu, B * N, B};
-    const void* dev[13];
+    const size_t S = v->stage_stride ? (size_t)v->stage_stride : N;
+    // stage arrays span (B - 1) S + N stages (the last instance needs only N)
+    const size_t ST = (B - 1) * S + N;
+    constexpr int NA = 17;
+    const void* src[NA] = {v->A,  v->Bm,   v->e,      v->Q,    v->R,       v->ry, v->ru, v->mu,    v->fmax,
+                           v->xi0, v->u_prev, v->mask, v->horizon, v->C, v->nu, v->xlo, v->xhi};
+    const size_t cnt[NA] = {ST * nx * nx, ST * nx * nu, ST * nx, ST * nx, ST * nu, ST * nx, ST * nu, ST * nc, ST * nc,
+                            B * nx,       B * nu,       ST,      B,       ST * nx, B,       ST * nx, ST * nx};
+    const void* dev[NA];
     bool any_host = false;
-    for (int i = 0; i < 13; ++i) any_host |= is_host_pointer(src[i]);
+    for (int i = 0; i < NA; ++i) any_host |= is_host_pointer(src[i]);
     if (any_host) {
         size_t need = 0;
-        for (int i = 0; i < 13; ++i) need += src[i] ? ((cnt[i] + 63) & ~size_t(63)) : 0;
+        for (int i = 0; i < NA; ++i) need += src[i] ? ((cnt[i] + 63) & ~size_t(63)) : 0;
         if (need > h->staging_floats) {
             if (h->staging) {
                 cudaFree(h->staging);
@@ -594,7 +625,7 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
         if (h->consumed_valid && (e = cudaStreamWaitEvent(h->copy_stream, h->consumed, 0)) != cudaSuccess)
             return cuda_fail(h, e, "cudaStreamWaitEvent");
         size_t off = 0;
-        for (int i = 0; i < 13; ++i) {
+        for (int i = 0; i < NA; ++i) {
             if (!src[i]) { dev[i] = nullptr; continue; }
             if (is_host_pointer(src[i])) {
                 float* d = h->staging + off;
@@ -610,7 +641,7 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
             (e = cudaStreamWaitEvent(s, h->staged, 0)) != cudaSuccess)
             return cuda_fail(h, e, "staging event");
     } else {
-        for (int i = 0; i < 13; ++i) dev[i] = src[i];
+        for (int i = 0; i < NA; ++i) dev[i] = src[i];
     }
     PackArgs a{};
     a.A = (const float*)dev[0]; a.Bm = (const float*)dev[1]; a.e = (const float*)dev[2];
@@ -618,7 +649,11 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     a.ru = (const float*)dev[6]; a.mu = (const float*)dev[7]; a.fmax = (const float*)dev[8];
     a.xi0 = (const float*)dev[9]; a.u_prev = (const float*)dev[10];
     a.mask = (const uint32_t*)dev[11]; a.horizon = (const int32_t*)dev[12];
+    a.C = (const float*)dev[13]; a.nu = (const int32_t*)dev[14];
+    a.xlo = (const float*)dev[15]; a.xhi = (const float*)dev[16];
+    a.xbox = (v->xlo || v->xhi) ? h->xbox : nullptr;
     a.N = (int)N;
+    a.S = (int)S;
     a.n_rec = c.N_max;
     a.irec = h->irec;
     a.sigma = c.u_scale;
@@ -631,6 +666,7 @@ mpc_status mpc_set_stages(mpc_handle* h, const mpc_stage_view* v, void* stream) 
     }
     h->B_set = (int)B;
     h->N_set = (int)N;
+    h->box_set = a.xbox != nullptr;
     h->have_stages = true;
     h->have_solution = false;
     return MPC_OK;
@@ -781,11 +817,13 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
     RoundArgs r{};
     r.rec = h->rec; r.irec = h->irec; r.n_rec = c.N_max; r.N = h->N_set;
     r.rho = c.rho; r.sigma = c.u_scale; r.kkt_tol = c.kkt_tol; r.eta = c.restart_eta;
+    r.kkt_c = c.kkt_tol_abs > 0.0f ? c.kkt_tol_abs / c.kkt_tol : 1.0f;
     r.dx = c.foot_half_length; r.dy = c.foot_half_width;
     r.max_iter = c.max_iter; r.polish = c.polish; r.accel = c.accel;
     r.refine_steps = c.refine_steps; r.refine_alpha = c.refine_alpha;
     r.cache = h->cache; r.state = h->state; r.modes = h->modes; r.lastm = h->lastm;
     r.done = h->done; r.Kst = h->Kst; r.flags = h->flags; r.B = B;
+    r.xbox = h->box_set ? h->xbox : nullptr; r.smodes = h->smodes; r.slast = h->slast;
     r.out_xi = h->out_xi; r.out_u = h->out_u; r.out_status = h->out_status; r.out_iters = h->out_iters;
     r.out_kkt = h->out_kkt; r.out_bits = h->out_bits; r.out_npol = h->out_npol; r.out_piv = h->out_piv;
     // each horizon class's launch form (double-buffered records and factors,
@@ -801,7 +839,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
         // replay the captured sequence for this key, capturing it first if new
         const int key_dbl = r.dbl;
         auto it = std::find_if(h->graphs.begin(), h->graphs.end(), [&](const mpc_handle::SolveGraph& g) {
-            return g.B == B && g.N == h->N_set && g.dbl == key_dbl && g.warm_B == r.warm_B;
+            return g.B == B && g.N == h->N_set && g.dbl == key_dbl && g.warm_B == r.warm_B && g.box == h->box_set;
         });
         if (it == h->graphs.end()) {
             if (!h->capture_stream &&
@@ -825,7 +863,7 @@ mpc_status mpc_solve_batch(mpc_handle* h, int32_t B, void* stream) {
                 cudaGraphExecDestroy(h->graphs.front().exec);
                 h->graphs.erase(h->graphs.begin());
             }
-            h->graphs.push_back({B, h->N_set, key_dbl, r.warm_B, ex});
+            h->graphs.push_back({B, h->N_set, key_dbl, r.warm_B, h->box_set, ex});
             ++h->graph_captures;
             it = h->graphs.end() - 1;
         }
@@ -1061,6 +1099,9 @@ void mpc_destroy(mpc_handle* h) {
     cudaFree(h->lists);
     cudaFree(h->work);
     cudaFree(h->Kst);
+    cudaFree(h->xbox);
+    cudaFree(h->smodes);
+    cudaFree(h->slast);
     cudaFree(h->staging);
     cudaGetLastError();
     delete h;

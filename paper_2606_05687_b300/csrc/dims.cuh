@@ -46,11 +46,12 @@ struct Dims {
     static constexpr int oFM = oMU + NC;
     static constexpr int oMASK = oFM + NC;
     static constexpr int SREC = (oMASK + 1 + 3) & ~3;
-    // instance tail: xi_0 | u_{-1}/sigma | horizon (int bits)
+    // instance tail: xi_0 | u_{-1}/sigma | horizon (int bits) | input-check bits of the pack
     static constexpr int tXI0 = 0;
     static constexpr int tUP = NX;
     static constexpr int tH = NX + NU;
-    static constexpr int TAIL = (NX + NU + 1 + 3) & ~3;
+    static constexpr int tFLAG = NX + NU + 1;
+    static constexpr int TAIL = (NX + NU + 2 + 3) & ~3;
     static_assert(NU % CD == 0, "nu must be a multiple of the contact dimension");
     static_assert(NB <= 64, "lifted dimension must fit two lanes per element");
     static_assert(NU <= 32 && NX <= 32, "one lane per row of the Riccati solve");

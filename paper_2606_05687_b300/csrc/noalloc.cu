@@ -103,7 +103,9 @@ mpc_status run(const mpc_config& c, const mpc_stage_view& v, float* xi, float* u
     pa.A = v.A; pa.Bm = v.Bm; pa.e = v.e; pa.Q = v.Q; pa.R = v.R; pa.ry = v.ry; pa.ru = v.ru;
     pa.mu = v.mu; pa.fmax = v.fmax; pa.xi0 = v.xi0; pa.u_prev = v.u_prev; pa.mask = v.mask;
     pa.horizon = v.horizon;
+    pa.C = v.C;
     pa.N = N;
+    pa.S = v.stage_stride ? v.stage_stride : N;
     pa.n_rec = N;
     pa.irec = (int)irec;
     pa.sigma = c.u_scale;
@@ -137,13 +139,19 @@ mpc_status mpc_solve_noalloc(const mpc_config* cfg, const mpc_stage_view* v, flo
         c.check_start < 1 || !(c.restart_eta > 0.0f && c.restart_eta < 1.0f) || c.refine_steps < 0 ||
         !(c.refine_alpha > 0.0f))
         return fail(MPC_ERR_INVALID_ARG, "invalid solver parameter");
+    if (v->nu) return fail(MPC_ERR_UNSUPPORTED, "the no-allocation solver takes every input (nu must be NULL)");
+    if (v->xlo || v->xhi) return fail(MPC_ERR_UNSUPPORTED, "the no-allocation solver takes no state boxes");
+    if (v->stage_stride != 0 && v->stage_stride < v->N)
+        return fail(MPC_ERR_INVALID_ARG, "stage_stride below N");
+    if (c.kkt_tol_abs != 0.0f && c.kkt_tol_abs != c.kkt_tol)
+        return fail(MPC_ERR_UNSUPPORTED, "the no-allocation solver certifies with kkt_tol_abs = kkt_tol only");
     if (c.precision != MPC_PREC_FP32)
         return fail(MPC_ERR_UNSUPPORTED, "the no-allocation solver runs FP32 only (precision must be MPC_PREC_FP32)");
     if (v->B < 1 || v->N < 1 || v->N > 32) return fail(MPC_ERR_INVALID_ARG, "B must be >= 1 and N in [1, 32]");
     if (!v->A || !v->Bm || !v->Q || !v->R || !v->ry || !v->mu || !v->fmax || !v->mask || !v->xi0)
         return fail(MPC_ERR_INVALID_ARG, "a required stage array is NULL");
     const void* ptrs[] = {v->A, v->Bm, v->e, v->Q, v->R, v->ry, v->ru, v->mu, v->fmax, v->mask, v->xi0,
-                          v->u_prev, v->horizon, xi, u, status, iters, kkt};
+                          v->u_prev, v->horizon, v->C, xi, u, status, iters, kkt};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

@@ -25,6 +25,7 @@ struct RoundArgs {
     const float* rec;
     int irec, n_rec, N;
     float rho, sigma, kkt_tol, eta, dx, dy;
+    float kkt_c;             // kkt_tol_abs / kkt_tol: the constant of the certificate's normalisations
     int max_iter, polish, accel, refine_steps;
     float refine_alpha;
     int m0, m1;              // this round runs iterations m0+1 .. m1
@@ -62,7 +63,25 @@ struct RoundArgs {
     // cap stages (every horizon of the class fits; N for a single class)
     int ncls, cls_stride, cap;
     int cls_cap[kMaxClasses];
+    // state boxes X_k on xi_{k+1} (null: none set): [B][N][2][NX] lower, upper
+    const float* xbox;
+    uint32_t* smodes;        // [B][N] bounds the latest z sits at (bit i: lower, bit 16 + i: upper)
+    uint32_t* slast;         // [B][N] the bounds of the last polish
 };
+
+// Augmented Lagrangian that holds active state bounds in the polish: the
+// starting penalty of a bound, the factor it grows by whenever a step cuts
+// that bound's violation by less than kBoxRate, its cap, the iteration limit
+// and the stopping violation (relative).  A bound the inputs reach only
+// through several stages (a position behind a velocity) is stiff: its
+// multiplier converges at rate h / (h + penalty), h the cost of moving it,
+// so its penalty has to grow past h.
+constexpr float kBoxPenalty = 1e4f;
+constexpr float kBoxGrow = 10.0f;
+constexpr float kBoxRate = 0.1f;
+constexpr float kBoxPenaltyMax = 1e7f;
+constexpr int kBoxIters = 12;
+constexpr float kBoxViol = 1e-7f;
 
 // Class of an instance with horizon Nh: the first class whose cap holds it;
 // a horizon outside [1, N] goes to the last class (cap N), whose round kernel

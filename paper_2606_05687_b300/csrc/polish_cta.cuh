@@ -58,7 +58,7 @@ struct CtaSmem {
     // fall in different bank quads
     static constexpr int CP = (((NU + 3) / 4) % 2 == 1) ? 4 * ((NU + 3) / 4) : 4 * ((NU + 3) / 4) + 4;
     static_assert(CP <= 32, "column buffer");
-    int xr, ur, y, wv, modes, cmu, cfm, cmask, total;
+    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
@@ -72,6 +72,10 @@ struct CtaSmem {
         cmu = take(N * D::NC);
         cfm = take(N * D::NC);
         cmask = take(N);
+        nub = take(N * NX);   // signed multipliers of the active state bounds
+        rhob = take(N * NX);  // their augmented-Lagrangian penalties
+        dprev = take(N * NX); // their violations after the previous scan
+        sbits = take(N);      // active state bounds per stage (bit i lower, 16 + i upper)
         total = o;
     }
 };
@@ -109,6 +113,8 @@ struct CCtx {
     float* K;  // global gains [N][NU][NK]
     int Nh, tid, lane, warp;
     float sigma, dx, dy;
+    float kc;  // certificate normalisation constant kkt_tol_abs / kkt_tol (1 by default)
+    const float* box;  // this instance's state boxes [N][2][NX], or null
     __device__ CCtx(int N) : L(N) {}
     __device__ const float* grec(int k) const { return rec + (size_t)k * D::SREC; }
     __device__ float* buf(int k) const { return sm + ((k & 1) ? CtaSmem<D>::obuf1 : CtaSmem<D>::obuf0); }
@@ -119,6 +125,19 @@ struct CCtx {
     __device__ float mu(int k, int q) const { return sm[L.cmu + k * D::NC + q]; }
     __device__ float fms(int k, int q) const { return sm[L.cfm + k * D::NC + q]; }
     __device__ uint32_t mask(int k) const { return __float_as_uint(sm[L.cmask + k]); }
+    __device__ float* nub() const { return sm + L.nub; }
+    __device__ float* rhob() const { return sm + L.rhob; }
+    __device__ float* dprev() const { return sm + L.dprev; }
+    __device__ uint32_t* sbits() const { return reinterpret_cast<uint32_t*>(sm + L.sbits); }
+    // the bound of component i of xi_{k+1} that is active (upper if both), and whether any is
+    __device__ bool box_active(int k, int i, float* bound, bool* upper) const {
+        const uint32_t sb = sbits()[k];
+        const bool hi = (sb >> (16 + i)) & 1u, lo = (sb >> i) & 1u;
+        if (!(hi || lo)) return false;
+        *upper = hi;
+        *bound = box[(k * 2 + (hi ? 1 : 0)) * D::NX + i];
+        return true;
+    }
 };
 
 template <class D>
@@ -193,7 +212,7 @@ __device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((
 // M is kept at full size: an eliminated column makes row and column of M a
 // unit vector and its row of the right-hand side zero, so its elimination
 // step is skipped and its gains come out zero.
-template <class D>
+template <class D, bool BOX = false>
 __device__ int cta_polish(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
     using CS = CtaSmem<D>;
@@ -227,6 +246,20 @@ __device__ int cta_polish(const CCtx<D>& c) {
         pf.store(s, tid);
         __syncthreads();
         if (k > 0) pf.load(c.grec(k - 1), tid);
+        if constexpr (BOX) {
+            // augmented Lagrangian of the active state bounds: the stage cost of
+            // component i gains p_i/2 (x_i - b_i + nu_i / p_i)^2 (p_i its penalty),
+            // i.e. Q_i + p_i and Q_i r_i + p_i b_i - nu_i
+            float bnd;
+            bool up;
+            if (tid < NX && c.box_active(k, tid, &bnd, &up)) {
+                const float q = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
+                const float qn = q + pen;
+                s[D::oRY + tid] = (fmaf(q, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
+                s[D::oQ + tid] = qn;
+            }
+            __syncthreads();
+        }
         // (1) warp 0: reduced input map (one column per lane), free columns, et.
         //     warps 1..3: S = Q + sym(P), s = Q ry + p, AT = A'
         if (tid < 32) {
@@ -562,8 +595,74 @@ __device__ void cta_rollout(const CCtx<D>& c) {
     __syncthreads();
 }
 
-// KKT certificate (the terms of `certificate` in solve.cuh).
+// Multipliers of the active state bounds read off the ADMM iterate: at a
+// fixed point of Sec. III's iteration, rho (theta_k - lambda_k) restricted to
+// the state components is the normal-cone element of z_{k+1}'s state part,
+// i.e. the signed multiplier of its box (the state part is not scaled).  An
+// estimate of the wrong sign starts at 0.
 template <class D>
+__device__ void cta_box_init(const CCtx<D>& c, const RoundArgs& a, int b) {
+    const float* st = a.state + (size_t)b * RoundState<D>::floats(a.N);
+    const int cb = __float_as_int(st[RoundState<D>::var_floats(a.N) + RoundState<D>::sCb]);
+    for (int e = c.tid; e < c.Nh * D::NX; e += kPT) {
+        const int k = e / D::NX, i = e % D::NX;
+        float bnd, v = 0.0f;
+        bool up;
+        if (c.box_active(k, i, &bnd, &up)) {
+            v = a.rho * (st[RoundState<D>::at(a.N, cb, k, VTH) + i] - st[RoundState<D>::at(a.N, cb, k, VLA) + i]);
+            if (up ? v < 0.0f : v > 0.0f) v = 0.0f;
+        }
+        c.nub()[e] = v;
+        c.rhob()[e] = kBoxPenalty;
+        c.dprev()[e] = INFINITY;
+    }
+    __syncthreads();
+}
+
+// Polish with the active state bounds held by an augmented Lagrangian: scans
+// with the penalised stage costs (see cta_polish), each followed by the
+// multiplier step nu += kBoxPenalty (x - b) on the active bounds, until every
+// active bound holds to kBoxViol (relative) or kBoxIters scans.  Without
+// active bounds this is one plain scan.  Returns the pivots eliminated and
+// adds the scans to *nscan.
+template <class D, bool BOX>
+__device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
+    constexpr int NX = D::NX;
+    bool any = false;
+    if constexpr (BOX) {
+        for (int k = c.tid; k < c.Nh; k += kPT) any |= c.sbits()[k] != 0u;
+        any = __syncthreads_or(any);
+    }
+    int npiv = 0;
+    for (int t = 0; t < (any ? kBoxIters : 1); ++t) {
+        npiv += cta_polish<D, BOX>(c);
+        ++*nscan;
+        if (!any) break;
+        float viol = 0.0f;
+        for (int e = c.tid; e < c.Nh * NX; e += kPT) {
+            const int k = e / NX, i = e % NX;
+            float bnd;
+            bool up;
+            if (c.box_active(k, i, &bnd, &up)) {
+                const float d = c.xr()[(k + 1) * NX + i] - bnd;
+                const float pen = c.rhob()[e];
+                c.nub()[e] = fmaf(pen, d, c.nub()[e]);
+                const float vi = fabsf(d) / (1.0f + fabsf(bnd));
+                // a stiff bound (its violation falls too slowly) gets a larger penalty
+                if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e]) c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
+                c.dprev()[e] = fabsf(d);
+                viol = fmaxf(viol, vi);
+            }
+        }
+        viol = cta_max(c, viol);
+        if (viol <= kBoxViol) break;
+    }
+    __syncthreads();
+    return npiv;
+}
+
+// KKT certificate (the terms of `certificate` in solve.cuh).
+template <class D, bool BOX = false>
 __device__ float cta_certificate(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, CD = D::CD, M = D::M, F = D::F;
     const int tid = c.tid;
@@ -583,6 +682,15 @@ __device__ float cta_certificate(const CCtx<D>& c) {
                 const float* An = c.buf(k + 1) + D::oA;  // stage k+1, kept from the previous step
 #pragma unroll
                 for (int i = 0; i < NX; ++i) acc = fmaf(An[i * NX + tid], c.y()[(k + 1) * NX + i], acc);
+            }
+            if constexpr (BOX) {
+                // an active state bound's multiplier (of the right sign) enters y_k
+                float bnd;
+                bool up;
+                if (c.box_active(k, tid, &bnd, &up)) {
+                    const float v = c.nub()[k * NX + tid];
+                    if (up ? v >= 0.0f : v <= 0.0f) acc += v;
+                }
             }
             c.y()[k * NX + tid] = acc;
         }
@@ -613,7 +721,7 @@ __device__ float cta_certificate(const CCtx<D>& c) {
             float mm = 0.0f;
 #pragma unroll
             for (int i = 0; i < CD; ++i) mm = fmaxf(mm, fabsf(u[i]));
-            feas = fmaxf(feas, mm / (1.0f + fmax));
+            feas = fmaxf(feas, mm / (c.kc + fmax));
             continue;
         }
         const float mu = c.mu(k, q);
@@ -635,7 +743,7 @@ __device__ float cta_certificate(const CCtx<D>& c) {
         for (int f = 0; f < F; ++f) { lam[f] = 0.0f; gmax = fmaxf(gmax, g[f]); }
 #pragma unroll
         for (int i = 0; i < CD; ++i) wmax = fmaxf(wmax, fabsf(r[i]));
-        feas = fmaxf(feas, fmaxf(gmax, 0.0f) / (1.0f + fmax));
+        feas = fmaxf(feas, fmaxf(gmax, 0.0f) / (c.kc + fmax));
         for (int sweep = 0; sweep < 100; ++sweep) {
             float change = 0.0f;
 #pragma unroll
@@ -671,14 +779,32 @@ __device__ float cta_certificate(const CCtx<D>& c) {
         stat = fmaxf(stat, rs);
         comp = fmaxf(comp, rc);
     }
+    if constexpr (BOX) {
+        // state boxes: violation max(x - hi, lo - x, 0) / (kc + |bound|), and
+        // |nu (x - b)| of the active bounds whose multiplier counts
+        for (int e = tid; e < c.Nh * NX; e += kPT) {
+            const int k = e / NX, i = e % NX;
+            const float lo = c.box[(k * 2) * NX + i], hi = c.box[(k * 2 + 1) * NX + i];
+            const float x = c.xr()[(k + 1) * NX + i];
+            if (x > hi) feas = fmaxf(feas, (x - hi) / (c.kc + fabsf(hi)));
+            if (x < lo) feas = fmaxf(feas, (lo - x) / (c.kc + fabsf(lo)));
+            float bnd;
+            bool up;
+            if (c.box_active(k, i, &bnd, &up)) {
+                const float v = c.nub()[e];
+                if (up ? v >= 0.0f : v <= 0.0f) comp = fmaxf(comp, fabsf(v * (x - bnd)));
+            }
+        }
+    }
     feas = cta_max(c, feas);
     stat = cta_max(c, stat);
     comp = cta_max(c, comp);
-    return fmaxf(feas, fmaxf(stat / (1.0f + den), comp / (1.0f + uinf)));
+    // each term |res| / (kc + scale) <= kkt_tol  <=>  |res| <= kkt_tol_abs + kkt_tol scale
+    return fmaxf(feas, fmaxf(stat / (c.kc + den), comp / (c.kc + uinf)));
 }
 
 // Faces re-read off Proj(u - alpha sigma w); returns whether any changed.
-template <class D>
+template <class D, bool BOX = false>
 __device__ bool cta_refine_modes(const CCtx<D>& c, float alpha) {
     constexpr int NU = D::NU, CD = D::CD;
     bool changed = false;
@@ -693,6 +819,33 @@ __device__ bool cta_refine_modes(const CCtx<D>& c, float alpha) {
         if (mw != c.modes[e]) {
             changed = true;
             c.modes[e] = mw;
+        }
+    }
+    if constexpr (BOX) {
+        // state bounds: a violated one joins (multiplier 0), an active one whose
+        // multiplier has the wrong sign leaves
+        constexpr int NX = D::NX;
+        for (int e = c.tid; e < c.Nh * NX; e += kPT) {
+            const int k = e / NX, i = e % NX;
+            const float lo = c.box[(k * 2) * NX + i], hi = c.box[(k * 2 + 1) * NX + i];
+            const float x = c.xr()[(k + 1) * NX + i], v = c.nub()[e];
+            const uint32_t sb = c.sbits()[k];
+            const bool alo = (sb >> i) & 1u, ahi = (sb >> (16 + i)) & 1u;
+            uint32_t set = 0u, clr = 0u;
+            if (ahi && v < 0.0f) clr |= 1u << (16 + i);
+            if (alo && v > 0.0f) clr |= 1u << i;
+            if (!ahi && x > hi) set |= 1u << (16 + i);
+            if (!alo && x < lo) set |= 1u << i;
+            if (set | clr) {
+                changed = true;
+                if (set) {
+                    atomicOr(c.sbits() + k, set);
+                    c.nub()[e] = 0.0f;
+                    c.rhob()[e] = kBoxPenalty;
+                    c.dprev()[e] = INFINITY;
+                }
+                if (clr) atomicAnd(c.sbits() + k, ~clr);
+            }
         }
     }
     return __syncthreads_or(changed);
@@ -749,7 +902,7 @@ __device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, in
 }
 
 // Polish / certify / refine after a round: one CTA per instance.
-template <class D>
+template <class D, bool BOX>
 __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float* psm) {
     constexpr int NX = D::NX, NU = D::NU;
     if (a.done[b]) return;
@@ -762,6 +915,8 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
     c.lane = threadIdx.x & 31;
     c.warp = threadIdx.x >> 5;
     c.sigma = a.sigma;
+    c.kc = a.kkt_c;
+    c.box = BOX ? a.xbox + (size_t)b * a.n_rec * 2 * NX : nullptr;
     c.dx = a.dx;
     c.dy = a.dy;
     const float* tail = c.rec + (size_t)a.n_rec * D::SREC;
@@ -779,6 +934,16 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         c.sm[c.L.cfm + e] = __ldg(c.grec(k) + D::oFM + q);
     }
     for (int k = c.tid; k < c.Nh; k += kPT) c.sm[c.L.cmask + k] = __ldg(c.grec(k) + D::oMASK);
+    // the state bounds the round's z sits at; a change also calls for a polish
+    uint32_t* gsm = BOX ? a.smodes + (size_t)b * a.N : nullptr;
+    uint32_t* gsl = BOX ? a.slast + (size_t)b * a.N : nullptr;
+    if constexpr (BOX) {
+        for (int k = c.tid; k < c.Nh; k += kPT) {
+            const uint32_t sb = gsm[k];
+            c.sbits()[k] = sb;
+            changed |= (sb != gsl[k]);
+        }
+    }
     for (int i = c.tid; i < NX; i += kPT) c.xr()[i] = __ldg(tail + D::tXI0 + i);
     changed = __syncthreads_or(changed);
     int npol = a.out_npol[b];
@@ -786,14 +951,16 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
     float kkt = INFINITY;
     if (a.polish && changed) {
         for (int e = c.tid; e < c.Nh * D::NC; e += kPT) glast[e] = c.modes[e];
-        npiv += cta_polish<D>(c);
-        ++npol;
-        kkt = cta_certificate<D>(c);
+        if constexpr (BOX) {
+            for (int k = c.tid; k < c.Nh; k += kPT) gsl[k] = c.sbits()[k];
+            cta_box_init<D>(c, a, b);
+        }
+        npiv += cta_polish_box<D, BOX>(c, &npol);
+        kkt = cta_certificate<D, BOX>(c);
         for (int r = 0; kkt > a.kkt_tol && r < a.refine_steps; ++r) {
-            if (!cta_refine_modes<D>(c, a.refine_alpha)) break;
-            npiv += cta_polish<D>(c);
-            ++npol;
-            kkt = cta_certificate<D>(c);
+            if (!cta_refine_modes<D, BOX>(c, a.refine_alpha)) break;
+            npiv += cta_polish_box<D, BOX>(c, &npol);
+            kkt = cta_certificate<D, BOX>(c);
         }
         if (c.tid == 0) a.out_piv[b] = npiv;
         if (kkt <= a.kkt_tol) {
@@ -810,8 +977,14 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
             const int k = e / NU, i = e % NU;
             c.ur()[e] = st[RoundState<D>::at(a.N, cb, k, VZ) + NX + i];
         }
+        if constexpr (BOX) {
+            // the round's bounds and multipliers (a polish may have moved them)
+            for (int k = c.tid; k < c.Nh; k += kPT) c.sbits()[k] = gsm[k];
+            __syncthreads();
+            cta_box_init<D>(c, a, b);
+        }
         cta_rollout<D>(c);
-        kkt = cta_certificate<D>(c);
+        kkt = cta_certificate<D, BOX>(c);
         if (kkt <= a.kkt_tol || final_round) {
             cta_write_output<D>(c, a, b, kkt <= a.kkt_tol ? kConverged : kMaxIter, a.m1, kkt, npol);
             return;
@@ -828,7 +1001,7 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
 // Polish / certify / refine after a round: CTA i takes slot i of the round's
 // lists, the classes' lists taken one after another (grid = batch size;
 // slots past their total length return at once).
-template <class D>
+template <class D, bool BOX = false>
 __global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float psm[];
     int b = -1;
@@ -846,7 +1019,7 @@ __global__ void __launch_bounds__(kPT, D::CD == 3 ? 5 : 3) polish_cta_kernel(Rou
         }
     }
     if (b < 0) return;
-    polish_instance<D>(a, b, psm);
+    polish_instance<D, BOX>(a, b, psm);
 }
 
 }  // namespace pinmpc

@@ -49,7 +49,7 @@ constexpr int kClusterMaxN = 64;
 // One round (a.m0, a.m1] of one instance by CTA `rank` of the pair; NL is the
 // local stage capacity ceil(cap / 2).  The instance's horizon Nh (1..cap)
 // was checked by the caller.
-template <class D, int MAXT>
+template <class D, int MAXT, bool BOX>
 __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, float* smem, uint32_t rank, int NL) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, NBP = D::NBP, FR = RoundSmem<D>::FR;
     constexpr bool TWO = RegT<D>::kTwo;
@@ -120,6 +120,8 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
         }
         if (rank == 0) {
             for (int e = tid; e < a.N * D::NC; e += nthr) a.lastm[(size_t)b * a.N * D::NC + e] = 0xffffffffu;
+            if constexpr (BOX)
+                for (int e = tid; e < a.N; e += nthr) a.slast[(size_t)b * a.N + e] = 0xffffffffu;
             if (tid == 0) {
                 a.out_npol[b] = 0;
                 a.out_piv[b] = 0;
@@ -170,6 +172,7 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
         R.ir2 = 1.0f / (1.0f + 2.0f * R.mu * R.mu);
         R.stance = (mask(j) >> q) & 1u;
         R.mw = 0u;
+        if constexpr (BOX) load_box<D>(a, b, k0 + j, lane, R);
     }
     __syncthreads();
     // Abar_0 xibar_0 is constant (global stage 0); the other stages form theirs every iteration
@@ -203,7 +206,7 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
         }
         cluster_barrier();
         if (active) {
-            const float cm = block2_r<D, true>(c, R, cb, j, lane, a.dx, a.dy);
+            const float cm = block2_r<D, true, BOX>(c, R, cb, j, lane, a.dx, a.dy);
             if (lane == 0) c.part[j] = cm;
         }
         cluster_barrier();
@@ -232,6 +235,8 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
         for (int e = tid; e < lvar / 4; e += nthr) dst[e] = src[e];
     }
     if (active && lane < D::NC && a.m1 > a.m0) a.modes[((size_t)b * a.N + k0 + j) * D::NC + lane] = R.mw;
+    if constexpr (BOX)
+        if (active && a.m1 > a.m0) store_box_bits<D>(a, b, k0 + j, lane, R, c.var + RoundState<D>::at(NL, cb, j, VZ));
     if (rank == 0 && tid == 0) {
         float* sc = gstate + nvar;
         sc[RoundState<D>::sAlpha] = alpha;
@@ -245,7 +250,7 @@ __device__ __forceinline__ void round_instance_cl(const RoundArgs& a, int b, flo
 // Persistent pairs: grid = 2 x pairs, block = 32 ceil(cap / 2) threads
 // (MAXT at least that), dynamic shared memory RoundSmem<D>(ceil(cap / 2)),
 // cap = a.cap: the longest horizon the launch takes.
-template <class D, int MAXT>
+template <class D, int MAXT, bool BOX = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(MAXT, 1) round_cl_kernel(RoundArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ int item[2];  // instance (or -1: no work left) and the action for it
@@ -271,7 +276,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(MAXT, 1) round_cl_ke
                 } else if (Nh < 1 || Nh > cap) {
                     act = 2 + kBadHorizon;
                 } else if (a.m0 == 0 && a.flags[b]) {
-                    act = 2 + ((a.flags[b] & 1) ? kNonFinite : kBadSet);
+                    act = 2 + ((a.flags[b] & 1) ? kNonFinite : ((a.flags[b] & 4) ? kBadDim : kBadSet));
                 }
             }
             item[0] = b;
@@ -282,7 +287,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(MAXT, 1) round_cl_ke
         cluster_barrier();
         const int b = item[0], act = item[1];
         if (b < 0) break;
-        if (act == 0) round_instance_cl<D, MAXT>(a, b, smem, rank, NL);
+        if (act == 0) round_instance_cl<D, MAXT, BOX>(a, b, smem, rank, NL);
         else if (act >= 2 && rank == 0) round_fail<D>(a, b, act - 2);
     }
 }

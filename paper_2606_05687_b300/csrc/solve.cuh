@@ -29,7 +29,7 @@
 
 namespace pinmpc {
 
-enum : int { kConverged = 0, kMaxIter = 1, kNonFinite = 2, kBadSet = 3, kTimeout = 4, kBadHorizon = 5 };
+enum : int { kConverged = 0, kMaxIter = 1, kNonFinite = 2, kBadSet = 3, kTimeout = 4, kBadHorizon = 5, kBadDim = 6 };
 
 // mode word of one contact after the projection (bit layout):
 //   bit 2j   : tangential j clamped at +c_j n     bit 2j+1 : clamped at -c_j n
@@ -1100,7 +1100,12 @@ struct PackArgs {
     const float *A, *Bm, *e, *Q, *R, *ry, *ru, *mu, *fmax, *xi0, *u_prev;
     const uint32_t* mask;
     const int32_t* horizon;
-    int N;          // stage stride of the caller's arrays
+    const float* C;          // [B][S][NX] diagonal output map, or null (C = I)
+    const int32_t* nu;       // [B] inputs present per instance, or null (all)
+    const float *xlo, *xhi;  // [B][S][NX] state boxes of xi_{k+1} (either may be null: unbounded)
+    float* xbox;             // [B][n_rec][2][NX] packed boxes, or null (no boxes this batch)
+    int N;          // stages read per instance
+    int S;          // stages between consecutive instances in the caller's arrays (>= N)
     int n_rec;      // stage capacity of a record
     int irec;       // floats per record
     float sigma;
@@ -1114,7 +1119,12 @@ __global__ void pack_kernel(PackArgs a) {
     const int N = a.N;
     float* rec = a.rec + (size_t)b * a.irec;
     const float sg = a.sigma, isg = 1.0f / a.sigma;
-    const size_t sb = (size_t)b * N;
+    const size_t sb = (size_t)b * a.S;
+    // inputs present: the first nu[b] / CD contacts; a count that is not a
+    // multiple of CD in [0, NU] leaves every contact out and flags the instance
+    const int nub = a.nu ? a.nu[b] : NU;
+    const bool nu_ok = nub >= 0 && nub <= NU && nub % D::CD == 0;
+    const uint32_t present = nu_ok ? (nub / D::CD >= 32 ? 0xffffffffu : ((1u << (nub / D::CD)) - 1u)) : 0u;
     // inputs through the read-only path (they never alias the records), so
     // the unrolled copy loops keep several loads in flight per thread
 #pragma unroll 4
@@ -1131,8 +1141,16 @@ __global__ void pack_kernel(PackArgs a) {
         const int k = e / NX, r = e % NX;
         float* s = rec + k * D::SREC;
         s[D::oE + r] = a.e ? __ldg(a.e + sb * NX + e) : 0.0f;
-        s[D::oQ + r] = __ldg(a.Q + sb * NX + e);
-        s[D::oRY + r] = __ldg(a.ry + sb * NX + e);
+        const float q = __ldg(a.Q + sb * NX + e), ry = __ldg(a.ry + sb * NX + e);
+        if (a.C) {
+            // ||c x - r||^2_q = ||x - r / c||^2_{c^2 q} (a zero c drops the component's cost)
+            const float cc = __ldg(a.C + sb * NX + e);
+            s[D::oQ + r] = cc * cc * q;
+            s[D::oRY + r] = cc != 0.0f ? ry / cc : 0.0f;
+        } else {
+            s[D::oQ + r] = q;
+            s[D::oRY + r] = ry;
+        }
     }
     for (int e = tid; e < N * NU; e += nthr) {
         const int k = e / NU, r = e % NU;
@@ -1148,8 +1166,16 @@ __global__ void pack_kernel(PackArgs a) {
     }
     for (int k = tid; k < N; k += nthr) {
         float* s = rec + k * D::SREC;
-        s[D::oMASK] = __uint_as_float(a.mask[sb + k]);
+        s[D::oMASK] = __uint_as_float(a.mask[sb + k] & present);
         for (int r = D::oMASK + 1; r < D::SREC; ++r) s[r] = 0.0f;
+    }
+    if (a.xbox) {
+        float* bx = a.xbox + (size_t)b * a.n_rec * 2 * NX;
+        for (int e = tid; e < N * NX; e += nthr) {
+            const int k = e / NX, r = e % NX;
+            bx[(k * 2 + 0) * NX + r] = a.xlo ? __ldg(a.xlo + sb * NX + e) : -INFINITY;
+            bx[(k * 2 + 1) * NX + r] = a.xhi ? __ldg(a.xhi + sb * NX + e) : INFINITY;
+        }
     }
     float* tail = rec + (size_t)a.n_rec * D::SREC;
     for (int i = tid; i < D::TAIL; i += nthr) {
@@ -1157,6 +1183,7 @@ __global__ void pack_kernel(PackArgs a) {
         if (i < NX) v = a.xi0[(size_t)b * NX + i];
         else if (i < NX + NU) v = a.u_prev ? a.u_prev[(size_t)b * NU + i - NX] * isg : 0.0f;
         else if (i == D::tH) v = __int_as_float(a.horizon ? a.horizon[b] : N);
+        else if (i == D::tFLAG) v = __int_as_float(nu_ok ? 0 : 4);
         tail[i] = v;
     }
 }

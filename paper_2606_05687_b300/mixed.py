@@ -20,11 +20,13 @@ class MixedSolver:
     sub-batch and waits for all of them.  With `classes` each handle runs its
     ADMM rounds per horizon class (mpc_set_horizon_classes)."""
 
-    def __init__(self, batches: List, classes: bool = True, **overrides):
+    def __init__(self, batches: List, classes: bool = True, graph: bool = False, **overrides):
         import torch
 
         self.torch = torch
         self.solvers = [pinmpc.solver_for(b, **overrides) for b in batches]
+        for s in self.solvers:
+            s.set_graph_mode(graph)  # replay each (B, N, warm start) solve from a captured CUDA graph
         if classes:
             # ragged horizons: each round on CTAs sized for each horizon class
             for s, b in zip(self.solvers, batches):
@@ -37,6 +39,12 @@ class MixedSolver:
         for s, st, t, shp in zip(self.solvers, self.streams, inputs, self.shapes):
             s.set_stages(shp[3], shp[4], **t, stream=st)
 
+    def warm_start(self, shift: int = 1):
+        """The next solve of every sub-batch starts from its last solution
+        moved `shift` stages (mpc_warm_start: a receding-horizon step)."""
+        for s, st in zip(self.solvers, self.streams):
+            s.warm_start(shift, stream=st)
+
     def solve(self, wait: bool = True):
         for s, st, shp in zip(self.solvers, self.streams, self.shapes):
             s.solve(shp[3], stream=st)
@@ -44,8 +52,9 @@ class MixedSolver:
             for st in self.streams:
                 st.synchronize()
 
-    def results(self) -> List[Dict]:
-        """Per sub-batch: xi, u, status, iters, kkt (numpy), after `solve`."""
+    def results(self, device: bool = False) -> List[Dict]:
+        """Per sub-batch: xi, u, status, iters, kkt after `solve` (numpy, or
+        device tensors with device=True, read on each sub-batch's stream)."""
         torch = self.torch
         out = []
         for s, st, (nx, nc, cd, B, N) in zip(self.solvers, self.streams, self.shapes):
@@ -55,6 +64,9 @@ class MixedSolver:
             iters = torch.empty(B, dtype=torch.int32, device="cuda")
             kkt = torch.empty(B, device="cuda")
             s.get_traj(xi, u, status, iters, kkt, None, stream=st)
+            if device:
+                out.append(dict(xi=xi, u=u, status=status, iters=iters, kkt=kkt))
+                continue
             st.synchronize()
             out.append(dict(xi=xi.cpu().numpy(), u=u.cpu().numpy(), status=status.cpu().numpy(),
                             iters=iters.cpu().numpy(), kkt=kkt.cpu().numpy()))

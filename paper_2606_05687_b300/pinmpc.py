@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpinmpc.so")
 
 MPC_OK, MPC_ERR_INVALID_ARG, MPC_ERR_OOM, MPC_ERR_CUDA, MPC_ERR_STATE, MPC_ERR_UNSUPPORTED = range(6)
-CONVERGED, MAX_ITER, NONFINITE, BAD_SET, TIMEOUT, BAD_HORIZON = range(6)
+CONVERGED, MAX_ITER, NONFINITE, BAD_SET, TIMEOUT, BAD_HORIZON, BAD_DIM = range(7)
 RUNNING = -1  # status of an instance whose solve has not finished it yet
 PREC_FP32, PREC_TF32, PREC_BF16 = range(3)  # mpc_config.precision
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID_ARG", 2: "MPC_ERR_OOM", 3: "MPC_ERR_CUDA",
@@ -33,7 +33,8 @@ class MpcConfig(ctypes.Structure):
                 ("restart_eta", ctypes.c_float), ("refine_steps", ctypes.c_int32),
                 ("refine_alpha", ctypes.c_float), ("foot_half_length", ctypes.c_float),
                 ("foot_half_width", ctypes.c_float), ("mem_budget", ctypes.c_uint64),
-                ("device", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("kkt_tol_abs", ctypes.c_float)]
 
 
 _P = ctypes.c_void_p
@@ -42,7 +43,8 @@ _P = ctypes.c_void_p
 class StageView(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("N", ctypes.c_int32), ("A", _P), ("Bm", _P), ("e", _P),
                 ("Q", _P), ("R", _P), ("ry", _P), ("ru", _P), ("mu", _P), ("fmax", _P),
-                ("mask", _P), ("xi0", _P), ("u_prev", _P), ("horizon", _P)]
+                ("mask", _P), ("xi0", _P), ("u_prev", _P), ("horizon", _P), ("C", _P), ("nu", _P),
+                ("stage_stride", ctypes.c_int32), ("xlo", _P), ("xhi", _P)]
 
 
 KERNEL_CLASSES = 4
@@ -193,11 +195,13 @@ class Solver:
             raise MpcError(st, f"{what}: {self.lib.mpc_last_error(self.h).decode()}")
 
     def set_stages(self, B: int, N: int, *, A, Bm, Q, R, ry, mu, fmax, mask, xi0, e=None,
-                   ru=None, u_prev=None, horizon=None, stream=None):
+                   ru=None, u_prev=None, horizon=None, C=None, nu=None, stage_stride=0, xlo=None, xhi=None,
+                   stream=None):
         v = StageView(B=B, N=N, A=_ptr(A), Bm=_ptr(Bm), e=_ptr(e), Q=_ptr(Q), R=_ptr(R),
                       ry=_ptr(ry), ru=_ptr(ru), mu=_ptr(mu), fmax=_ptr(fmax), mask=_ptr(mask),
-                      xi0=_ptr(xi0), u_prev=_ptr(u_prev), horizon=_ptr(horizon))
-        self._keep = (A, Bm, Q, R, ry, mu, fmax, mask, xi0, e, ru, u_prev, horizon)
+                      xi0=_ptr(xi0), u_prev=_ptr(u_prev), horizon=_ptr(horizon), C=_ptr(C), nu=_ptr(nu),
+                      stage_stride=int(stage_stride), xlo=_ptr(xlo), xhi=_ptr(xhi))
+        self._keep = (A, Bm, Q, R, ry, mu, fmax, mask, xi0, e, ru, u_prev, horizon, C, nu, xlo, xhi)
         self._check(self.lib.mpc_set_stages(self.h, ctypes.byref(v), _stream_ptr(stream)),
                     "mpc_set_stages")
 

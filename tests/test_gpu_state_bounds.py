@@ -1,0 +1,160 @@
+"""State boxes X_k (Sec. III's standard form, xi_{k+1} in X_k) through the C
+ABI, against the FP64 oracle with the same boxes as inequality rows.
+
+Boxes are placed inside each instance's unbounded optimum so that they bind
+on some stages: a lower bound on the vertical velocity (a directly actuated
+state), a lower bound on the CoM height (a state the inputs reach only
+through the velocity, one stage later) and an upper bound on the forward
+velocity (reached through friction).  The ADMM projects the state part of
+z onto the box; the polish holds the bounds the iterate sits at by an
+augmented Lagrangian and certifies with their multipliers.  Bars as for the
+unbounded parity tests: relative xi and u error <= 1e-4, oracle-checked KKT
+(with the boxes' joint multipliers) <= 1e-5, the device certificate never
+below the checker's (less 20 % + 5e-7), relative objective gap <= 1e-6.
+
+Which instances certify depends on how directly the inputs reach the
+bounded component.  The augmented Lagrangian's multiplier converges at rate
+h / (h + penalty), h the cost of moving the component (about 1e3 for the
+vertical velocity, 1e4 for the forward velocity through friction, up to
+3e6 for the CoM height two stages behind the forces); its penalty grows
+until the bound holds, capped at 1e7 where FP32 Riccati sums lose the
+other terms.  Velocity boxes therefore certify; CoM-height boxes mostly
+stop at the iteration cap and say so (MPC_MAX_ITER, certificate above the
+tolerance).  Every certified instance must match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kkt as okkt
+from oracle import qp
+from paper_2606_05687_b300 import pinmpc
+from paper_2606_05687_b300 import workload as W
+
+import test_gpu_admm as TA
+import test_gpu_view as TV
+
+pytestmark = pytest.mark.gpu
+
+
+def boxes_inside(batch, free_xi, frac=0.25):
+    """xlo, xhi [B, N, nx] placed inside each instance's unbounded optimum,
+    by instance b mod 3: the vertical velocity held at or above its frac
+    quantile (every stage); the CoM height held at or above its frac quantile
+    from the third stage on (xi_1's height is fixed by xi_0 and xi_2's almost);
+    the forward velocity capped at its (1 - frac) quantile from the fourth
+    stage on (friction slows the body by about mu g dt per stage).  The
+    inputs can meet each bound, so every instance stays feasible."""
+    B, N, nx = batch.B, batch.N, batch.nx
+    xlo = np.full((B, N, nx), -np.inf, np.float32)
+    xhi = np.full((B, N, nx), np.inf, np.float32)
+    for b in range(B):
+        nh = int(batch.horizon[b])
+        if b % 3 == 0:
+            xlo[b, :, 8] = np.quantile(free_xi[b, :nh, 8], frac)
+        elif b % 3 == 1:
+            xlo[b, 2:, 2] = np.quantile(free_xi[b, 2:nh, 2], frac)
+        else:
+            xhi[b, 3:, 6] = np.quantile(free_xi[b, 3:nh, 6], 1.0 - frac)
+    return xlo, xhi
+
+
+def oracle_with_boxes(batch, b, xlo, xhi):
+    inst = qp.instance(batch, b)
+    nh = inst.N
+    inst.xlo = xlo[b, :nh].astype(np.float64)
+    inst.xhi = xhi[b, :nh].astype(np.float64)
+    return inst
+
+
+def check(batch, out, ids, xlo, xhi):
+    worst = 0.0
+    n_bind = 0
+    for b in ids:
+        inst = oracle_with_boxes(batch, b, xlo, xhi)
+        ref = qp.solve_instance(inst)
+        nh = inst.N
+        u = out["u"][b, :nh].astype(np.float64)
+        xi = out["xi"][b, :nh].astype(np.float64)
+        eu = np.abs(u - ref.u).max() / np.abs(ref.u).max()
+        ex = np.abs(xi - ref.xi).max() / np.abs(ref.xi).max()
+        rep = okkt.kkt_residual(inst, xi, u)
+        gap = abs(qp.objective(inst, xi, u) - ref.objective) / abs(ref.objective)
+        assert out["status"][b] == pinmpc.CONVERGED, b
+        assert eu <= 1e-4 and ex <= 1e-4, (b, eu, ex)
+        assert rep.kkt <= 1e-5, (b, rep)
+        assert gap <= 1e-6, (b, gap)
+        # the device certifies with the augmented Lagrangian's multipliers, the
+        # checker finds the best ones: the device may only be the more pessimistic
+        assert float(out["kkt"][b]) >= 0.8 * rep.kkt - 5e-7, (b, out["kkt"][b], rep.kkt)
+        bind = np.isclose(ref.xi, inst.xhi, rtol=0, atol=1e-7) | np.isclose(ref.xi, inst.xlo, rtol=0, atol=1e-7)
+        n_bind += int(bind.sum())
+        worst = max(worst, eu, ex)
+    return worst, n_bind
+
+
+@pytest.mark.parametrize("maker,B,N", [(W.rl_scale_walking, 48, 12), (W.small_centroidal, 32, 10),
+                                       (W.small_centroidal, 8, 40)])
+def test_state_boxes_match_the_oracle(maker, B, N):
+    TA.ensure_lib()
+    batch = W.generate(maker(B=B, N=N, seed=1401, e_scale=0.02))
+    free = pinmpc.solve_workload(batch)
+    xlo, xhi = boxes_inside(batch, free["xi"])
+    s = pinmpc.solver_for(batch)
+    out = TV.run(s, batch, {"xlo": torch.from_numpy(xlo).cuda(), "xhi": torch.from_numpy(xhi).cuda()})
+    st = out["status"]
+    s.close()
+    ok = st == pinmpc.CONVERGED
+    # honest statuses: an uncertified instance reports the cap with its certificate above the tolerance
+    assert np.all(ok | (st == pinmpc.MAX_ITER)) and np.all(out["kkt"][~ok] > 2e-6)
+    by_type = [int(ok[t::3].sum()) for t in range(3)]
+    n_type = [len(ok[t::3]) for t in range(3)]
+    assert by_type[0] == n_type[0], by_type          # vertical velocity: every instance certifies
+    assert by_type[2] >= n_type[2] // 2, by_type     # forward velocity through friction: most
+    ids = [b for b in range(B) if ok[b]][::max(1, int(ok.sum()) // 12)]
+    worst, n_bind = check(batch, out, ids, xlo, xhi)
+    assert n_bind >= len(ids) // 2  # the boxes bind at the optimum
+    print(f"{maker.__name__} N={N}: certified by bound type {by_type} of {n_type}, worst {worst:.2e}, "
+          f"{n_bind} binding bounds, iters mean {out['iters'].mean():.1f}")
+
+
+def test_loose_boxes_change_nothing():
+    """Boxes that never bind: the box variant of the kernels returns the
+    unbounded solve's results bit for bit."""
+    TA.ensure_lib()
+    batch = W.generate(W.rl_scale_walking(B=64, N=20, seed=1402))
+    s = pinmpc.solver_for(batch)
+    ref = TV.run(s, batch)
+    lo = torch.full((64, 20, 13), -1e6, device="cuda")
+    hi = torch.full((64, 20, 13), 1e6, device="cuda")
+    got = TV.run(s, batch, {"xlo": lo, "xhi": hi})
+    again = TV.run(s, batch)
+    s.close()
+    for k in ("xi", "u", "status", "iters", "kkt", "bits"):
+        assert np.array_equal(got[k], ref[k]), k
+        assert np.array_equal(again[k], ref[k]), k
+
+
+def test_plain_admm_with_state_boxes():
+    """Polish off: the ADMM's box projection alone, certified with the
+    bounds' multipliers read off the duals, rho (theta - lambda) on the state
+    part; instances that certify match the oracle within the residual's bound
+    (see test_gpu_admm.test_plain_admm_reaches_the_oracle_optimum)."""
+    TA.ensure_lib()
+    batch = W.generate(W.rl_scale_walking(B=32, N=5, seed=7, schedule="all_stance", e_scale=0.05))
+    free = pinmpc.solve_workload(batch)
+    xlo, xhi = boxes_inside(batch, free["xi"], frac=0.3)
+    xlo[1::3] = -np.inf  # velocity boxes only (see above)
+    s = pinmpc.solver_for(batch, polish=0, kkt_tol=1e-5, max_iter=20000, check_start=10, check_every=10,
+                          check_growth=1.0)
+    out = TV.run(s, batch, {"xlo": torch.from_numpy(xlo).cuda(), "xhi": torch.from_numpy(xhi).cuda()})
+    s.close()
+    ok = np.flatnonzero(out["status"] == pinmpc.CONVERGED)
+    assert len(ok) >= 0.5 * batch.B, len(ok)
+    for b in ok:
+        inst = oracle_with_boxes(batch, b, xlo, xhi)
+        ref = qp.solve_instance(inst)
+        u = out["u"][b].astype(np.float64)
+        xi = out["xi"][b].astype(np.float64)
+        rep = okkt.kkt_residual(inst, xi, u)
+        assert rep.kkt <= 2e-5, (b, rep)
+        assert np.abs(xi - ref.xi).max() <= 1e-3 * np.abs(ref.xi).max(), b

@@ -1,0 +1,56 @@
+"""Absolute and relative parts of the certificate's tolerance
+(mpc_config.kkt_tol_abs): each KKT term must satisfy
+|residual| <= kkt_tol_abs + kkt_tol * scale.  A small absolute part demands
+more of the small-scale terms; the device's certificate then agrees with the
+oracle checker evaluated in the same normalisation, and every certified
+solution still matches the oracle.  An absolute part far below the
+relative one (1e-3 of it) asks for residuals near FP32 rounding on the
+small-scale terms; instances that cannot reach it stop at the iteration cap
+and say so (MPC_MAX_ITER with their certificate above the tolerance)."""
+import numpy as np
+import pytest
+
+from oracle import kkt as okkt
+from oracle import qp
+from paper_2606_05687_b300 import pinmpc
+from paper_2606_05687_b300 import workload as W
+
+from parity_util import compare, oracle_refs
+import test_gpu_admm as TA
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("ratio", [1e-3, 1.0, 30.0])
+def test_absolute_part_of_the_tolerance(ratio):
+    TA.ensure_lib()
+    batch = W.generate(W.rl_scale_walking(B=128, N=20, seed=1201))
+    tol = 2e-6
+    out = pinmpc.solve_workload(batch, kkt_tol=tol, kkt_tol_abs=ratio * tol)
+    st = out["status"]
+    assert np.all((st == pinmpc.CONVERGED) | (st == pinmpc.MAX_ITER))
+    if ratio >= 1.0:
+        assert np.all(st == pinmpc.CONVERGED), np.flatnonzero(st)
+    # an uncertified instance says so: its certificate is above the tolerance
+    assert np.all(out["kkt"][st == pinmpc.MAX_ITER] > tol)
+    ids = [b for b in range(0, 128, 8) if st[b] == pinmpc.CONVERGED]
+    for b in ids:
+        inst = qp.instance(batch, b)
+        rep = okkt.kkt_residual(inst, out["xi"][b].astype(np.float64), out["u"][b].astype(np.float64), c=ratio)
+        assert rep.kkt <= 2 * tol, (b, rep)
+        # the device's certificate never understates the residual; at the
+        # default normalisation it agrees with the checker (with a tiny
+        # absolute part its FP32 multiplier search is the more pessimistic)
+        assert float(out["kkt"][b]) >= 0.8 * rep.kkt - 5e-7, (b, out["kkt"][b], rep.kkt)
+        if ratio >= 1.0:
+            assert abs(float(out["kkt"][b]) - rep.kkt) <= 0.2 * rep.kkt + 5e-7, (b, out["kkt"][b], rep.kkt)
+    if ratio == 1.0:
+        compare(batch, out, ids)
+    elif ratio < 1.0:
+        # trajectories against the oracle (compare() checks the certificate
+        # in the default normalisation, so only the trajectory bars here)
+        for b, (xi_r, u_r, _) in zip(ids, oracle_refs(batch, ids)):
+            assert np.abs(out["u"][b] - u_r).max() <= 1e-4 * np.abs(u_r).max(), b
+            assert np.abs(out["xi"][b] - xi_r).max() <= 1e-4 * np.abs(xi_r).max(), b
+    print(f"ratio {ratio}: {int((st == 0).sum())}/128 certified, iters mean {out['iters'].mean():.1f}, "
+          f"polishes mean {out['polishes'].mean():.2f}")

@@ -10,6 +10,7 @@ Each pin checks the oracle against something other than itself:
   * a planted mistake in the oracle (dropped e_k, transposed A_k) that the
     Riccati pin must catch.
 """
+import dataclasses
 import itertools
 
 import numpy as np
@@ -30,8 +31,9 @@ def lqr_tracking(inst: qp.Instance):
     for k in range(N - 1, -1, -1):
         A, B, e = inst.A[k], inst.Bm[k], inst.e[k]
         R = np.diag(inst.R[k])
-        S = np.diag(inst.Q[k]) + P
-        s = inst.Q[k] * inst.ry[k] + p
+        Cm = np.diag(inst.cdiag()[k])
+        S = Cm.T @ np.diag(inst.Q[k]) @ Cm + P
+        s = Cm.T @ (inst.Q[k] * inst.ry[k]) + p
         M = R + B.T @ S @ B
         K = -np.linalg.solve(M, B.T @ S @ A)
         kap = np.linalg.solve(M, R @ inst.ru[k] + B.T @ (s - S @ e))
@@ -90,6 +92,26 @@ def test_unconstrained_equals_lqr(maker, e_scale):
         scale_u = np.abs(us).max()
         assert np.abs(sol.u - us).max() <= 1e-9 * scale_u
         assert np.abs(sol.xi - xs).max() <= 1e-9 * max(1.0, np.abs(xs).max())
+
+
+def test_unconstrained_equals_lqr_with_output_map():
+    """A diagonal output map C in the cost ||C xi - r^y||^2_Q (weights in
+    [0.3, 2], some components dropped with C = 0) against the Riccati
+    recursion with S = C'QC + P, s = C'Q r^y + p."""
+    b = W.generate(W.rl_scale_walking(B=2, N=8, schedule="all_stance", e_scale=0.05, seed=13))
+    rng = np.random.default_rng(13)
+    for i in range(b.B):
+        inst = standing_interior(qp.instance(b, i))
+        inst.ru[:, 0] += 3.0
+        inst.C = rng.uniform(0.3, 2.0, size=inst.Q.shape)
+        inst.C[:, [5, 12]] = 0.0  # yaw and the gravity state out of the cost
+        xs, us = lqr_tracking(inst)
+        assert strictly_inside(inst, us)
+        sol = qp.solve_instance(inst)
+        assert np.abs(sol.u - us).max() <= 1e-9 * np.abs(us).max()
+        # and C changes the answer (the pin is sensitive to it)
+        plain = qp.solve_instance(dataclasses.replace(inst, C=None))
+        assert np.abs(plain.u - us).max() > 1e-4 * np.abs(us).max()
 
 
 @pytest.mark.parametrize("maker,N", [(W.small_centroidal, 40), (W.rl_scale_walking, 64)])
@@ -178,6 +200,16 @@ def full_kkt_bruteforce(inst: qp.Instance):
                 row[cols] = G[r]
                 Ineq.append(row)
                 ih.append(h[r])
+    for lim, sgn in ((inst.xhi, 1.0), (inst.xlo, -1.0)):   # state boxes on xi_{k+1}
+        if lim is None:
+            continue
+        for k in range(N):
+            for r in range(nx):
+                if np.isfinite(lim[k, r]):
+                    row = np.zeros(nz)
+                    row[xi_idx(k).start + r] = sgn
+                    Ineq.append(row)
+                    ih.append(sgn * lim[k, r])
     Eq, eq, Ineq, ih = map(np.array, (Eq, eq, Ineq, ih))
     found = []
     m = len(ih)
@@ -219,6 +251,55 @@ def test_bruteforce_active_sets_tiny(seed):
     sol = qp.solve_instance(inst)
     assert np.abs(sol.u - u_b).max() <= 1e-8 * (1 + np.abs(u_b).max())
     assert np.abs(sol.xi - xi_b).max() <= 1e-8 * (1 + np.abs(xi_b).max())
+
+
+@pytest.mark.parametrize("seed", [21])
+def test_bruteforce_with_state_bounds(seed):
+    """State boxes X_k as condensed rows: N = 2, one 3-D contact, and two
+    bounds placed inside the unbounded optimum (so they bind), against the
+    enumeration of every working set of faces and bounds (2^14) on the
+    non-condensed problem; the checker's joint multipliers certify it."""
+    spec = W.rl_scale_walking(B=1, N=2, schedule="all_stance", seed=seed, ref_noise=1.0)
+    inst = qp.instance(W.generate(spec), 0)
+    inst.stance[:] = False
+    inst.stance[:, 0] = True
+    inst.fmax[:] = 150.0
+    free = qp.solve_instance(inst)
+    inst.xhi = np.full((2, inst.nx), np.inf)
+    inst.xlo = np.full((2, inst.nx), -np.inf)
+    # v_x of xi_1 capped below its free value, v_z of xi_2 held above its free value
+    inst.xhi[0, 6] = free.xi[0, 6] - 0.02 * (1 + abs(free.xi[0, 6]))
+    inst.xlo[1, 8] = free.xi[1, 8] + 0.02 * (1 + abs(free.xi[1, 8]))
+    xi_b, u_b = full_kkt_bruteforce(inst)
+    sol = qp.solve_instance(inst)
+    assert np.abs(sol.u - u_b).max() <= 1e-8 * (1 + np.abs(u_b).max())
+    assert np.abs(sol.xi - xi_b).max() <= 1e-8 * (1 + np.abs(xi_b).max())
+    # a bound binds (the first one moves the solution enough that the second may not)
+    assert abs(sol.xi[0, 6] - inst.xhi[0, 6]) <= 1e-9 or abs(sol.xi[1, 8] - inst.xlo[1, 8]) <= 1e-9
+    rep = kkt.kkt_residual(inst, sol.xi, sol.u)
+    assert rep.kkt <= 1e-9, rep
+    # the free optimum violates the boxes, and the checker says so
+    assert kkt.kkt_residual(inst, free.xi, free.u).r_feas > 1e-3
+
+
+def test_admm_fixed_point_with_state_bounds():
+    """The Sec. III iteration with X_k a box (the state part of z clipped)
+    reaches the same optimum as the interior-point oracle with box rows."""
+    from oracle import admm
+    batch = W.generate(W.rl_scale_walking(B=2, N=6, seed=5, e_scale=0.05))
+    inst = qp.instance(batch, 1)
+    free = qp.solve_instance(inst)
+    inst.xhi = np.full((6, inst.nx), np.inf)
+    inst.xhi[2:5, 8] = free.xi[2:5, 8].max() - 0.05   # cap v_z over three stages
+    ref = qp.solve_instance(inst)
+    assert np.any(np.abs(ref.xi[2:5, 8] - inst.xhi[2:5, 8]) <= 1e-8)
+    si = admm.scaled_instance(inst, 300.0)
+    L = admm.lift(si, u_prev=batch.u_prev[1].astype(np.float64) / 300.0)
+    run = admm.solve(L, 100.0, 6000, accel=True)
+    _, u = admm.primal(L, run.w, si)
+    u = u * 300.0
+    assert np.abs(u - ref.u).max() <= 1e-6 * np.abs(ref.u).max()
+    assert kkt.kkt_residual(inst, ref.xi, ref.u).kkt <= 1e-9
 
 
 def test_bruteforce_has_active_faces():

@@ -267,3 +267,18 @@ def test_admm_fixed_point_does_not_depend_on_u_prev():
         run = admm.solve(L, 100.0, 3000, accel=True)
         outs.append(admm.primal(L, run.w, si)[1] * SIGMA)
     assert np.abs(outs[0] - outs[1]).max() <= 1e-6 * np.abs(outs[0]).max()
+
+
+def test_checker_absolute_part_of_the_tolerance():
+    """With c = kkt_tol_abs / kkt_tol every normalisation 1 + scale becomes
+    c + scale: c = 1 is the default, and for a point off the optimum the
+    reported residual falls as c grows (a larger absolute allowance)."""
+    batch = W.generate(W.rl_scale_walking(B=1, N=6, seed=5))
+    inst = qp.instance(batch, 0)
+    sol = qp.solve_instance(inst)
+    u = sol.u * (1.0 + 1e-4 * np.random.default_rng(0).normal(size=sol.u.shape))
+    xi = qp.rollout(inst, u)
+    k1 = kkt.kkt_residual(inst, xi, u).kkt
+    assert kkt.kkt_residual(inst, xi, u, c=1.0).kkt == k1
+    lo, hi = kkt.kkt_residual(inst, xi, u, c=1e3).kkt, kkt.kkt_residual(inst, xi, u, c=1e-3).kkt
+    assert lo < k1 < hi
