@@ -63,9 +63,9 @@ KERNEL_HEADERS = {
 }
 MEASURED_TRAFFIC = {
     # the polish kernel's round-0 launch (all 4096 instances), one ncu capture
-    "polish:797eff1fed1d6180": 290403072,
+    "polish:2f8e1ab51a46ca3d": 292908288,
     # the round kernel's round-0 launch, one ncu capture
-    "round:9b74afa9b31dcda1": 437087232,
+    "round:0e74ee356f5a63b2": 440452096,
 }
 
 
@@ -543,6 +543,9 @@ def run_gpu(args):
                           **mi_over(args))
         serve_load(srv, poisson_arrivals(0.7 * value, 0.2, B, seed=SEED + 1))  # warm-up
         served = serve_load(srv, poisson_arrivals(0.7 * value, 1.0, B, seed=SEED))
+        # saturation: requests offered at 1.5x the batch figure, so batches fill
+        # and the server runs at its capacity (every request still answered)
+        served["saturation"] = serve_load(srv, poisson_arrivals(1.5 * value, 1.0, B, seed=SEED + 2))
         srv.close()
 
     landmark = None

@@ -8,8 +8,8 @@ input buffers (on the handle's stream), and enqueues set_stages / solve /
 get_traj there; a CUDA event marks the batch done.  Several handles keep
 several batches in flight, so a batch forms while others run.  Each
 request's latency runs from its arrival to the host observing its batch's
-event.  Requests are kept in arrays (a batch is a contiguous run of the
-queue), so the host loop costs per batch, not per request.  With
+event.  Requests are kept in arrays and batches are formed with vectorized
+index operations, so the host loop costs per batch, not per request.  With
 `early` (the default), a request is answered when the round that certifies
 its instance ends, not when its whole batch does: the library records an
 event after each round (mpc_set_round_events), a side stream copies the
@@ -26,9 +26,10 @@ request is the environment's next MPC step), environments with a state
 are placed first in their batch, and `reset(envs)` makes the next request
 of those environments cold (a new episode).  Two requests of one
 environment in the same batch both start from its state before the batch.
-A batch that loads a row another handle's batch saved waits for that save
-on the device, so an environment's requests see its states in request
-order whichever handles serve them.  With a device-memory budget the store
+A request whose environment is in a batch still in flight waits in the
+queue (keeping its place) until that batch retires and its state is saved,
+so an environment's requests see its states in request order whichever
+handles serve them; the others go ahead.  With a device-memory budget the store
 may hold fewer rows than environments; rows are then reclaimed least
 recently used, never while a batch in flight uses them, and an environment
 whose row was reclaimed starts cold.
@@ -57,7 +58,7 @@ def handle_bytes(workspace: int, B_max: int, N: int, nx: int, nu: int, env_input
     b = workspace
     b += sum(_rounded(B_max * v) for v in env_input_bytes.values())
     b += _rounded(B_max * N * nu * 4) + _rounded(B_max * N * nx * 4) + 2 * _rounded(B_max * 4)
-    b += _rounded(B_max * 4) + _rounded(B_max * 8) + _rounded(B_max * 4)  # idx (int32, int64), save idx
+    b += _rounded(B_max * 8) + _rounded(2 * B_max * 4)  # index vectors: environments, load and save rows
     return b
 
 
@@ -96,6 +97,7 @@ class WarmRows:
     environment whose row is reclaimed starts its next request cold."""
 
     def __init__(self, n_env: int, rows: int):
+        self.direct = rows >= n_env  # a row per environment: row e is environment e's
         self.row_of = np.full(n_env, -1, np.int64)
         self.env_of = np.full(rows, -1, np.int64)
         self.last_use = np.zeros(rows, np.int64)
@@ -106,6 +108,8 @@ class WarmRows:
     def acquire(self, envs: np.ndarray, has_state: np.ndarray) -> np.ndarray:
         """Rows for the environments of one batch (pinned); environments whose
         row had to be taken get has_state cleared."""
+        if self.direct:
+            return envs
         self.clock += 1
         rows = self.row_of[envs].copy()
         need = np.unique(envs[rows < 0])
@@ -132,7 +136,8 @@ class WarmRows:
         return rows
 
     def release(self, rows: np.ndarray):
-        np.subtract.at(self.pins, rows, 1)
+        if not self.direct:
+            np.subtract.at(self.pins, rows, 1)
 
 
 class BatchServer:
@@ -197,7 +202,13 @@ class BatchServer:
                         kkt=torch.empty(B_max, dtype=torch.float32, device=self.device))
             status_host = torch.empty(B_max, dtype=torch.int32).pin_memory()
             h = dict(solver=solver, stream=torch.cuda.Stream(self.device), inputs=inputs,
-                     outs=outs, status_host=status_host, busy=None, event=None, perm=None)
+                     outs=outs, status_host=status_host, busy=None, event=None, perm=None,
+                     # index vectors of a batch: environments (gather), and warm-state
+                     # rows to load then rows to save (-1: none), page-locked staging
+                     env_pin=torch.empty(B_max, dtype=torch.int64).pin_memory(),
+                     env_dev=torch.empty(B_max, dtype=torch.int64, device=self.device),
+                     row_pin=torch.empty(2 * B_max, dtype=torch.int32).pin_memory(),
+                     row_dev=torch.empty(2 * B_max, dtype=torch.int32, device=self.device))
             if early:
                 n_rounds = len(pinmpc.round_schedule(cfg))
                 side = torch.cuda.Stream(self.device)
@@ -217,19 +228,22 @@ class BatchServer:
             self.store = torch.zeros((warm_rows, rows), dtype=torch.float32, device=self.device)
             self.has_state = np.zeros(n_env, dtype=bool)
             self.rows = WarmRows(n_env, warm_rows)
-            # handle whose batch last saved each store row (-1: none); a batch
-            # that loads the row waits for that handle's save first
-            self.last_writer = np.full(warm_rows, -1, np.int64)
-            for h in self.handles:
-                h["save_event"] = None
+            self.slot_of = np.zeros(n_env, np.int64)  # scratch: an environment's last slot in a batch
         cap = 1 << 16
         self.env = np.zeros(cap, np.int64)
         self.t_arrival = np.zeros(cap)
         self.t_done = np.full(cap, np.nan)
         self.status = np.full(cap, -1, np.int32)
         self.n = 0          # requests submitted
-        self.head = 0       # first request not yet dispatched
+        self.head = 0       # first request not yet looked at by the dispatcher
+        # requests passed over because their environment's previous batch was
+        # still in flight (its saved state not yet final), oldest first
+        self.deferred = np.zeros(0, np.int64)
         self.batches = 0
+        if warm_shift is not None:
+            # the batch (serial number) that last took each environment, while in flight
+            self.env_batch = np.full(n_env, -1, np.int64)
+            self.deferrals = 0
         self.results: Dict[int, dict] = {}
         self.keep_results = False
 
@@ -255,7 +269,7 @@ class BatchServer:
 
     @property
     def queued(self) -> int:
-        return self.n - self.head
+        return self.n - self.head + len(self.deferred)
 
     def busy(self) -> bool:
         return any(h["busy"] is not None for h in self.handles)
@@ -265,13 +279,43 @@ class BatchServer:
         if self.warm_shift is not None:
             self.has_state[np.atleast_1d(np.asarray(envs, np.int64))] = False
 
+    def _take(self) -> np.ndarray:
+        """Request ids of the next batch, first-in first-out among those that
+        may go: with warm state, a request whose environment is in a batch
+        still in flight waits (its state is saved when that batch ends) and
+        keeps its place ahead of later requests."""
+        if self.warm_shift is None:
+            lo = self.head
+            self.head = min(self.n, lo + self.B_max)
+            return np.arange(lo, self.head)
+        free = self.env_batch < 0
+        d_ok = free[self.env[self.deferred]]
+        take = self.deferred[d_ok][:self.B_max]
+        kept = np.concatenate([self.deferred[d_ok][self.B_max:], self.deferred[~d_ok]])
+        need = self.B_max - len(take)
+        parts, wait = [take], [kept]
+        while need > 0 and self.head < self.n:
+            chunk = np.arange(self.head, min(self.n, self.head + 2 * need))
+            ok = free[self.env[chunk]]
+            pos = np.flatnonzero(ok)
+            if len(pos) > need:  # stop after the need-th eligible request
+                chunk, ok = chunk[:pos[need - 1] + 1], ok[:pos[need - 1] + 1]
+            parts.append(chunk[ok])
+            wait.append(chunk[~ok])
+            self.head = int(chunk[-1]) + 1
+            need -= int(ok.sum())
+        out = np.concatenate(parts)
+        self.deferred = np.sort(np.concatenate(wait))
+        self.deferrals += sum(len(w) for w in wait[1:])
+        return out
+
     def _dispatch(self, h):
         torch = self.torch
-        lo = self.head
-        hi = min(self.n, lo + self.B_max)
-        self.head = hi
-        B = hi - lo
-        envs = self.env[lo:hi]
+        reqs = self._take()
+        B = len(reqs)
+        if B == 0:
+            return
+        envs = self.env[reqs]
         perm = None
         n_warm = 0
         if self.warm_shift is not None:
@@ -281,43 +325,43 @@ class BatchServer:
             envs = envs[perm]
             n_warm = int(warm.sum())
         rows = None
+        # the batch's index vectors go up in one asynchronous copy from this
+        # handle's page-locked staging (free again: the handle's last batch
+        # has retired), before anything of the batch is enqueued -- a copy from
+        # pageable memory would block the host until the stream reached it
+        h["env_pin"][:B] = torch.from_numpy(envs)
         if self.warm_shift is not None:
             rows = self.rows.acquire(envs, self.has_state)  # pinned until the batch retires
+            # one writer per row: an environment with several requests in the
+            # batch saves from its last slot only
+            slots = np.arange(B)
+            self.slot_of[envs] = slots  # repeated environments: the last slot's write stays
+            save = np.where(self.slot_of[envs] == slots, rows, -1)
+            h["row_pin"][:B] = torch.from_numpy(rows.astype(np.int32))
+            h["row_pin"][self.B_max:self.B_max + B] = torch.from_numpy(save.astype(np.int32))
         with torch.cuda.stream(h["stream"]):
-            idx64 = torch.from_numpy(envs).to(self.device, non_blocking=True)
+            h["env_dev"][:B].copy_(h["env_pin"][:B], non_blocking=True)
+            if self.warm_shift is not None:
+                h["row_dev"].copy_(h["row_pin"], non_blocking=True)
+            idx64 = h["env_dev"][:B]
             for k in STAGE_KEYS:
                 torch.index_select(self.pool[k], 0, idx64, out=h["inputs"][k][:B])
         view = {k: h["inputs"][k][:B] for k in STAGE_KEYS}
         s = h["solver"]
         s.set_stages(B, self.N, **view, stream=h["stream"])
-        me = self.handles.index(h)
         if self.warm_shift is not None:
-            with torch.cuda.stream(h["stream"]):
-                ridx = torch.from_numpy(rows.astype(np.int32)).to(self.device, non_blocking=True)
+            ridx = h["row_dev"][:B]
+            sidx = h["row_dev"][self.B_max:self.B_max + B]
         if n_warm:
-            # rows saved by batches on other handles: their saves come first
-            for w in np.unique(self.last_writer[rows[:n_warm]]):
-                if w >= 0 and w != me and self.handles[w]["save_event"] is not None:
-                    h["stream"].wait_event(self.handles[w]["save_event"])
+            # every row was last saved by a batch that has retired (its
+            # environment waited in the queue for that), so no device wait is needed
             s.load_state(self.store, ridx, n_warm, stream=h["stream"])
             self.warm_loads += n_warm
         s.solve(B, stream=h["stream"])
         if self.warm_shift is not None:
-            # one writer per row: an environment with several requests in the
-            # batch saves from its last slot only
-            save = np.full(B, -1, np.int32)
-            _, last = np.unique(envs[::-1], return_index=True)
-            keep = B - 1 - last
-            save[keep] = rows[keep]
-            with torch.cuda.stream(h["stream"]):
-                sidx = torch.from_numpy(save).to(self.device, non_blocking=True)
             s.save_state(self.store, sidx, B, shift=self.warm_shift, stream=h["stream"])
-            ev_save = torch.cuda.Event()
-            ev_save.record(h["stream"])
-            h["save_event"] = ev_save
             self.has_state[envs] = True
-            self.last_writer[rows] = me
-            h["idx_keep"] = (idx64, ridx, sidx)
+            self.env_batch[envs] = self.batches
         h["rows"] = rows
         o = h["outs"]
         if self.early:
@@ -333,19 +377,21 @@ class BatchServer:
             h["status_host"][:B].copy_(o["status"][:B], non_blocking=True)
         ev = torch.cuda.Event()
         ev.record(h["stream"])
-        h["busy"], h["event"], h["perm"] = (lo, hi), ev, perm
+        h["busy"], h["event"], h["perm"] = reqs, ev, perm
+        h["serial"] = self.batches
         self.batches += 1
 
     def _answer_early(self, h, now):
         """Retire the requests whose instances the rounds copied so far finished."""
-        lo, hi = h["busy"]
-        order = h["perm"] if h["perm"] is not None else np.arange(hi - lo)
+        reqs = h["busy"]
+        # slot i holds request reqs[order[i]]
+        order = reqs[h["perm"]] if h["perm"] is not None else reqs
         while h["next_round"] < len(h["round_events"]) and h["round_copied"][h["next_round"]].query():
-            st = h["round_status"][h["next_round"]][:hi - lo].numpy()
+            st = h["round_status"][h["next_round"]][:len(reqs)].numpy()
             new = (st != pinmpc.RUNNING) & ~h["answered"]
             if new.any():
                 now = self.clock() if now is None else now
-                req = lo + order[new]
+                req = order[new]
                 self.t_done[req] = now
                 self.status[req] = st[new]
                 h["answered"] |= new
@@ -353,19 +399,25 @@ class BatchServer:
         return now
 
     def _retire(self, h, now):
-        lo, hi = h["busy"]
-        # slot i holds request lo + order[i]
-        order = h["perm"] if h["perm"] is not None else np.arange(hi - lo)
-        late = ~h["answered"] if self.early else np.ones(hi - lo, dtype=bool)
-        self.t_done[lo + order[late]] = now
-        self.status[lo + order] = h["status_host"][:hi - lo].numpy()
+        reqs = h["busy"]
+        B = len(reqs)
+        # slot i holds request order[i]
+        order = reqs[h["perm"]] if h["perm"] is not None else reqs
+        late = ~h["answered"] if self.early else np.ones(B, dtype=bool)
+        self.t_done[order[late]] = now
+        self.status[order] = h["status_host"][:B].numpy()
         if self.keep_results:
-            o = {k: h["outs"][k][:hi - lo].cpu().numpy() for k in ("u", "xi", "kkt")}
-            for i in range(hi - lo):
-                self.results[lo + int(order[i])] = {k: o[k][i] for k in o}
+            o = {k: h["outs"][k][:B].cpu().numpy() for k in ("u", "xi", "kkt")}
+            for i in range(B):
+                self.results[int(order[i])] = {k: o[k][i] for k in o}
         if h.get("rows") is not None:
             self.rows.release(h["rows"])
             h["rows"] = None
+        if self.warm_shift is not None:
+            # its environments may go again (their states are saved)
+            envs = self.env[reqs]
+            mine = self.env_batch[envs] == h["serial"]
+            self.env_batch[envs[mine]] = -1
         h["busy"], h["event"], h["perm"] = None, None, None
 
     def step(self):
@@ -495,6 +547,7 @@ def fleet_load(server, hz: float = 50.0, duration: float = 1.0, warmup: float = 
             "offered_ticks_per_s": counts["ticks"] / duration,
             "requests": int(win.sum()), "skipped_ticks": counts["skipped"], "resets": counts["resets"],
             "answered_per_s": done_in / duration,
+            "deferred": int(getattr(server, "deferrals", 0)),
             "certified": int(np.sum(server.status[lo:hi][win] == 0)),
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None}
