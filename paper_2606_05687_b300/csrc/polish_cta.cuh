@@ -370,9 +370,12 @@ __device__ int cta_polish(const CCtx<D>& c) {
         //     PB pivots (columns p0 .. p0 + PB - 1) per step, by two warps
         //     (warps 0-1 or 2-3 by CTA parity, so co-resident CTAs spread this
         //     phase over the SM's schedulers), thread j holding all NU entries
-        //     of column j in registers.  Step (fully unrolled, so every
-        //     register index is fixed; skipped uniformly when the whole block
-        //     is eliminated): the block's owners publish their columns into a
+        //     of column j in registers.  Step (a rolled loop: the rows are
+        //     held in rotated order, so the block's pivot rows are always the
+        //     first four registers and every register index is fixed, which
+        //     keeps the scan's code small enough for the instruction caches;
+        //     skipped uniformly when the whole block is eliminated, apart
+        //     from the rotation): the block's owners publish their columns into a
         //     double-buffered set, then every column solves the PB x PB pivot
         //     block for its block rows, M_bb y = x_b (Gaussian elimination,
         //     no pivoting: the block is SPD), and takes x -= M_.b y, x_b = y
@@ -388,11 +391,15 @@ __device__ int cta_polish(const CCtx<D>& c) {
             static_assert(NU % PB == 0, "pivot blocks tile the inputs");
             float* pcb = sm + CS::opcb;
             const bool act = gj < W;
-            float xc[4 * (CP / 4)];
+            // rows held in rotated order: before block pq, register 4 t + i
+            // holds row 4 (pq + t) + i (mod NU), so the block's pivot rows are
+            // always registers 0..3 and the block loop need not be unrolled
+            constexpr int NQ = NU / PB;
+            float xc[NU];
             {
                 const float4* c4 = reinterpret_cast<const float4*>(MC + (act ? gj : 0) * CP);
 #pragma unroll
-                for (int q = 0; q < CP / 4; ++q) {
+                for (int q = 0; q < NQ; ++q) {
                     const float4 t4 = c4[q];
                     xc[4 * q + 0] = t4.x;
                     xc[4 * q + 1] = t4.y;
@@ -401,27 +408,29 @@ __device__ int cta_polish(const CCtx<D>& c) {
                 }
             }
             int bsel = 0;
-#pragma unroll
-            for (int pq = 0; pq < NU / PB; ++pq) {
+#pragma unroll 1
+            for (int pq = 0; pq < NQ; ++pq) {
                 const int p0 = PB * pq;
                 if ((fmask >> p0) & ((1u << PB) - 1u)) {
                     float* buf = pcb + bsel * (PB * 32);
                     if (gj >= p0 && gj < p0 + PB) {
-                        float* dst = buf + (gj - p0) * 32;
+                        float4* dst = reinterpret_cast<float4*>(buf + (gj - p0) * 32);
 #pragma unroll
-                        for (int q = 0; q < CP / 4; ++q)
-                            reinterpret_cast<float4*>(dst)[q] =
-                                make_float4(xc[4 * q], xc[4 * q + 1], xc[4 * q + 2], xc[4 * q + 3]);
+                        for (int q = 0; q < NQ; ++q) dst[q] = make_float4(xc[4 * q], xc[4 * q + 1], xc[4 * q + 2], xc[4 * q + 3]);
                     }
                     asm volatile("bar.sync 1, 64;" ::: "memory");
                     // m[i][j] = M[p0 + i][p0 + j] (column j of the block), y = x_b
                     float m[PB][PB], y[PB];
 #pragma unroll
-                    for (int i = 0; i < PB; ++i) {
-                        y[i] = xc[p0 + i];
-#pragma unroll
-                        for (int j = 0; j < PB; ++j) m[i][j] = buf[j * 32 + p0 + i];
+                    for (int j = 0; j < PB; ++j) {
+                        const float4 t4 = reinterpret_cast<const float4*>(buf + j * 32)[0];
+                        m[0][j] = t4.x;
+                        m[1][j] = t4.y;
+                        m[2][j] = t4.z;
+                        m[3][j] = t4.w;
                     }
+#pragma unroll
+                    for (int i = 0; i < PB; ++i) y[i] = xc[i];
 #pragma unroll
                     for (int i = 0; i < PB; ++i) {
                         const float ip = rcp_approx(m[i][i]);
@@ -441,20 +450,28 @@ __device__ int cta_polish(const CCtx<D>& c) {
                         y[i] = v * rcp_approx(m[i][i]);
                     }
 #pragma unroll
-                    for (int q = 0; q < CP / 4; ++q) {
+                    for (int q = 1; q < NQ; ++q) {
 #pragma unroll
                         for (int j = 0; j < PB; ++j) {
                             const float4 cj = reinterpret_cast<const float4*>(buf + j * 32)[q];
-                            if (4 * q + 0 < NU) xc[4 * q + 0] = fmaf(-cj.x, y[j], xc[4 * q + 0]);
-                            if (4 * q + 1 < NU) xc[4 * q + 1] = fmaf(-cj.y, y[j], xc[4 * q + 1]);
-                            if (4 * q + 2 < NU) xc[4 * q + 2] = fmaf(-cj.z, y[j], xc[4 * q + 2]);
-                            if (4 * q + 3 < NU) xc[4 * q + 3] = fmaf(-cj.w, y[j], xc[4 * q + 3]);
+                            xc[4 * q + 0] = fmaf(-cj.x, y[j], xc[4 * q + 0]);
+                            xc[4 * q + 1] = fmaf(-cj.y, y[j], xc[4 * q + 1]);
+                            xc[4 * q + 2] = fmaf(-cj.z, y[j], xc[4 * q + 2]);
+                            xc[4 * q + 3] = fmaf(-cj.w, y[j], xc[4 * q + 3]);
                         }
                     }
 #pragma unroll
-                    for (int i = 0; i < PB; ++i) xc[p0 + i] = y[i];
+                    for (int i = 0; i < PB; ++i) xc[i] = y[i];
                     bsel ^= 1;
                 }
+                // rotate by one block: registers 0..3 move to the end
+                float t0 = xc[0], t1 = xc[1], t2 = xc[2], t3 = xc[3];
+#pragma unroll
+                for (int i = 0; i < NU - PB; ++i) xc[i] = xc[i + PB];
+                xc[NU - 4] = t0;
+                xc[NU - 3] = t1;
+                xc[NU - 2] = t2;
+                xc[NU - 1] = t3;
             }
             // (5) gains to K16 (scan) and to global memory (rollout)
             if (act && gj >= NU) {
