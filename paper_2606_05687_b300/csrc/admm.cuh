@@ -392,18 +392,18 @@ __device__ __forceinline__ float block2_r(const RCtx<D>& c, StageRegs<D>& R, int
     return warp_sum(cm);
 }
 
-// In-place Gauss-Jordan inverse of an SPD matrix held one row per lane pair
-// (row r = lane/2 in lanes 2r, 2r+1; lanes past the last row duplicate it);
-// no pivoting, the matrix is SPD.
+// In-place Gauss-Jordan inverses (no pivoting: the matrices are SPD) of two
+// matrices at once, one per half warp: lane (m, r) = (lane / 16, lane % 16) holds row r of matrix m (rows past
+// NX duplicate the last one).  Every pivot row is broadcast within its half.
 template <class D>
-__device__ __forceinline__ void gj_inverse_rows(int lane, float (&row)[D::NX]) {
+__device__ __forceinline__ void gj_inverse_two(int lane, float (&row)[D::NX]) {
     constexpr int NX = D::NX;
-    const int r = min(lane >> 1, NX - 1);
+    const int base = lane & 16, r = min(lane & 15, NX - 1);
 #pragma unroll
     for (int p = 0; p < NX; ++p) {
         float prow[NX];
 #pragma unroll
-        for (int cc = 0; cc < NX; ++cc) prow[cc] = __shfl_sync(0xffffffffu, row[cc], 2 * p);
+        for (int cc = 0; cc < NX; ++cc) prow[cc] = __shfl_sync(0xffffffffu, row[cc], base + p);
         const float piv = 1.0f / prow[p];
         const float fp = row[p] * piv;
         const bool mine = (r == p);
@@ -416,32 +416,46 @@ __device__ __forceinline__ void gj_inverse_rows(int lane, float (&row)[D::NX]) {
     }
 }
 
-// Row r of  dg I + T diag(d) T'  over the columns i >= i0 of T = [A B] (lane
-// pair (r, h) sums the columns i = i0 + h, i0 + h + 2, ...; the pair's halves
-// are combined), then its in-place Gauss-Jordan inverse.  Rows are held one
-// per lane pair; lanes past the last row duplicate it.
+// Row r = min(lane % 16, NX - 1) of  dg I + T diag(w) T'  with T = [A B]
+// given as its columns tT[i][0..15] (zero-padded), i < NB, and the column
+// weights w (0 drops a column).  The terms go into two partial sums by the
+// parity of i - i0 (i0 = NX for m = 0, the first column of B; 0 for m = 1),
+// added at the end; both halves of the warp run the same loop.
 template <class D>
-__device__ __forceinline__ void gram_inverse(const float* sj, const float* d, float dg, int i0, int lane,
-                                             float (&row)[D::NX]) {
-    constexpr int NX = D::NX, NU = D::NU, NB = D::NB;
-    const int r = min(lane >> 1, NX - 1), h = lane & 1;
+__device__ __forceinline__ void gram_rows(const float* tT, const float* w, float dg, int lane, float (&row)[D::NX]) {
+    constexpr int NX = D::NX, NB = D::NB;
+    const int r = min(lane & 15, NX - 1);
+    const int i_start = (lane < 16) ? (NX & 1) : 0;
+    float a0[NX], a1[NX];
 #pragma unroll
-    for (int cc = 0; cc < NX; ++cc) row[cc] = 0.0f;
-#pragma unroll 2
-    for (int i = i0 + h; i < NB; i += 2) {
-        const float* col = i < NX ? sj + D::oA + i : sj + D::oB + (i - NX);
-        const int stride = i < NX ? NX : NU;
-        const float tri = col[r * stride] * (d ? d[i] : 1.0f);
+    for (int cc = 0; cc < NX; ++cc) a0[cc] = a1[cc] = 0.0f;
+    auto term = [&](int i, float (&acc)[NX]) {
+        const float4* col = reinterpret_cast<const float4*>(tT + i * 16);
+        float cv[16];
 #pragma unroll
-        for (int cc = 0; cc < NX; ++cc) row[cc] = fmaf(tri, col[cc * stride], row[cc]);
+        for (int q = 0; q < 4; ++q) {
+            const float4 t4 = col[q];
+            cv[4 * q] = t4.x;
+            cv[4 * q + 1] = t4.y;
+            cv[4 * q + 2] = t4.z;
+            cv[4 * q + 3] = t4.w;
+        }
+        const float tri = tT[i * 16 + r] * w[i];
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) acc[cc] = fmaf(tri, cv[cc], acc[cc]);
+    };
+    for (int t = 0; t < (NB + 1) / 2; ++t) {
+        const int i = i_start + 2 * t;
+        if (i < NB) term(i, a0);
+        if (i + 1 < NB) term(i + 1, a1);
     }
 #pragma unroll
     for (int cc = 0; cc < NX; ++cc) {
-        row[cc] += __shfl_xor_sync(0xffffffffu, row[cc], 1);
+        row[cc] = a0[cc] + a1[cc];
         if (cc == r) row[cc] += dg;
     }
-    gj_inverse_rows<D>(lane, row);
 }
+
 
 // Precision of the factor kernel's Gram products T diag(d) T' (mpc_config.precision).
 enum : int { kPrecFP32 = 0, kPrecTF32 = 1, kPrecBF16 = 2 };
@@ -457,16 +471,15 @@ __device__ __forceinline__ uint32_t to_bf16x2(float lo, float hi) {
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// The same matrix as gram_inverse, with the Gram product on the tensor cores
+// The Gram product of gram_rows (T diag(d) T' over the columns i >= i0) on the tensor cores
 // (warp-level mma.sync, FP32 accumulation): TF32 operands (m16n8k8) or BF16
 // operands (m16n8k16).  M = the NX rows of T (padded to 16), N = the same 16
 // (two 8-column tiles), K = the columns i0 .. NB-1 (padded to the MMA's K);
 // A[m][k] = T[m][i0 + k], B[k][n] = d[i0 + k] T[n][i0 + k].  The 16 x 16
-// result goes through the warp's scratch `sg` (16 x 17 floats) into the row
-// layout of the inversion, which stays FP32.
+// result goes to the warp's scratch `sg` (16 x 17 floats), from which the
+// rows of the inversion (FP32) are read.
 template <class D, int PREC>
-__device__ __forceinline__ void gram_inverse_mma(const float* sj, const float* d, float dg, int i0, int lane,
-                                                 float* sg, float (&row)[D::NX]) {
+__device__ __forceinline__ void gram_mma(const float* sj, const float* d, int i0, int lane, float* sg) {
     constexpr int NX = D::NX, NU = D::NU, NB = D::NB, GP = 17;
     const int g = lane >> 2, t = lane & 3;
     auto T = [&](int rr, int cc) -> float {
@@ -516,12 +529,6 @@ __device__ __forceinline__ void gram_inverse_mma(const float* sj, const float* d
         sg[(g + 8) * GP + nt * 8 + 2 * t] = acc[nt][2];
         sg[(g + 8) * GP + nt * 8 + 2 * t + 1] = acc[nt][3];
     }
-    __syncwarp();
-    const int r = min(lane >> 1, NX - 1);
-#pragma unroll
-    for (int cc = 0; cc < NX; ++cc) row[cc] = sg[r * GP + cc] + (cc == r ? dg : 0.0f);
-    __syncwarp();
-    gj_inverse_rows<D>(lane, row);
 }
 
 // Per-stage factors of the ADMM round, one warp per (instance, stage):
@@ -549,7 +556,10 @@ __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a)
     static_assert(NX <= 16, "the tensor-core Gram covers 16 rows");
     __shared__ __align__(16) float s_rec[kFactorWarps][D::SREC];
     __shared__ __align__(16) float s_d[kFactorWarps][NBP];
-    __shared__ float s_g[PREC == kPrecFP32 ? 1 : kFactorWarps][PREC == kPrecFP32 ? 1 : 16 * 17];
+    // FP32: T = [A B] as columns (16-float rows, zero-padded) and the two
+    // Grams' column weights; tensor cores: the two 16 x 17 Gram products
+    constexpr bool F32 = PREC == kPrecFP32;
+    __shared__ __align__(16) float s_t[kFactorWarps][F32 ? NB * 16 + 2 * NBP : 2 * 16 * 17];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kFactorWarps + warp;
     if (gw >= a.B * a.N) return;  // whole warps leave; the kernel has no CTA barrier
@@ -586,32 +596,44 @@ __global__ void __launch_bounds__(32 * kFactorWarps) factor_kernel(FactorArgs a)
     badset = __any_sync(0xffffffffu, badset);
     if (lane == 0 && (bad || badset || packbits)) atomicOr(a.flags + b, (bad ? 1 : 0) | (badset ? 2 : 0) | packbits);
     float* gc = a.cache + (size_t)b * RoundSmem<D>::cache_floats(a.N);
-    const int r = lane >> 1;
+    // half warp m computes matrix m: S_j (m = 0, the Gram of B's columns plus
+    // I) and W_j (m = 1, the Gram of T D'^{-1} plus I/rho; stage 0 has none),
+    // one row per lane, then both are inverted in one pass
+    const int m = lane >> 4, r = lane & 15;
+    const float dg = m ? 1.0f / a.rho : 1.0f;
+    float* st = s_t[warp];
     float row[NX];
-    auto store = [&](int m) {
-        if (r < NX && !(lane & 1)) {
-            float4* dst = reinterpret_cast<float4*>(gc + ((j * 2 + m) * NX + r) * FR);
-#pragma unroll
-            for (int q = 0; q < FR / 4; ++q) {
-                const int c0 = 4 * q;
-                dst[q] = make_float4(c0 < NX ? row[c0] : 0.0f, c0 + 1 < NX ? row[c0 + 1] : 0.0f,
-                                     c0 + 2 < NX ? row[c0 + 2] : 0.0f, c0 + 3 < NX ? row[c0 + 3] : 0.0f);
-            }
+    if constexpr (F32) {
+        float* w = st + NB * 16;
+        for (int e = lane; e < NB * 16; e += 32) {
+            const int i = e >> 4, cc = e & 15;
+            st[e] = cc < NX ? (i < NX ? sr[D::oA + cc * NX + i] : sr[D::oB + cc * D::NU + i - NX]) : 0.0f;
         }
-    };
-    if constexpr (PREC == kPrecFP32) {
-        gram_inverse<D>(sr, nullptr, 1.0f, NX, lane, row);
+        for (int i = lane; i < NBP; i += 32) {
+            w[i] = (i >= NX && i < NB) ? 1.0f : 0.0f;
+            w[NBP + i] = (j >= 1 && i < NB) ? dd[i] : 0.0f;
+        }
+        __syncwarp();
+        gram_rows<D>(st, w + m * NBP, dg, lane, row);
     } else {
-        gram_inverse_mma<D, PREC>(sr, nullptr, 1.0f, NX, lane, s_g[warp], row);
+        gram_mma<D, PREC>(sr, nullptr, NX, lane, st);
+        if (j >= 1) gram_mma<D, PREC>(sr, dd, 0, lane, st + 16 * 17);
+        __syncwarp();
+        const float* g = st + m * 16 * 17;
+        const int rr = min(r, NX - 1);
+        const bool none = m == 1 && j == 0;
+#pragma unroll
+        for (int cc = 0; cc < NX; ++cc) row[cc] = (none ? 0.0f : g[rr * 17 + cc]) + (cc == rr ? dg : 0.0f);
     }
-    store(0);
-    if (j >= 1) {
-        if constexpr (PREC == kPrecFP32) {
-            gram_inverse<D>(sr, dd, 1.0f / a.rho, 0, lane, row);
-        } else {
-            gram_inverse_mma<D, PREC>(sr, dd, 1.0f / a.rho, 0, lane, s_g[warp], row);
+    gj_inverse_two<D>(lane, row);
+    if (r < NX && (m == 0 || j >= 1)) {
+        float4* dst = reinterpret_cast<float4*>(gc + ((j * 2 + m) * NX + r) * FR);
+#pragma unroll
+        for (int q = 0; q < FR / 4; ++q) {
+            const int c0 = 4 * q;
+            dst[q] = make_float4(c0 < NX ? row[c0] : 0.0f, c0 + 1 < NX ? row[c0 + 1] : 0.0f,
+                                 c0 + 2 < NX ? row[c0 + 2] : 0.0f, c0 + 3 < NX ? row[c0 + 3] : 0.0f);
         }
-        store(1);
     }
 }
 

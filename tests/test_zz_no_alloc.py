@@ -5,13 +5,14 @@ step with a fixed memory pool, a real-time loop kept clear of the allocator).
 It must give the same answers as the regular handle-based entry point
 (mpc_set_stages + mpc_solve_batch + mpc_get_traj), within the parity
 tolerance of the other GPU tests, on two calls in a row that share its fixed
-scratch array.  This file is collected last on purpose."""
+scratch array, and meet the parity bars against the FP64 oracle directly.
+This file is collected last on purpose."""
 import numpy as np
 import pytest
 
 from paper_2606_05687_b300 import workload as W
 
-from parity_util import KKT_TOL, REL_TRAJ
+from parity_util import KKT_TOL, REL_TRAJ, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +40,8 @@ def _noalloc(P, batch):
     cfg = P.default_config(batch.nx, batch.nc, batch.contact_dim, B, N)
     P.solve_noalloc(cfg, B, N, **t, xi=xi, u=u, status=st, iters=it, kkt=kk)
     torch.cuda.synchronize()
-    return dict(xi=xi.cpu().numpy(), u=u.cpu().numpy(), status=st.cpu().numpy(), kkt=kk.cpu().numpy())
+    return dict(xi=xi.cpu().numpy(), u=u.cpu().numpy(), status=st.cpu().numpy(), kkt=kk.cpu().numpy(),
+                iters=it.cpu().numpy())
 
 
 def test_no_alloc_matches_regular_entry_point_twice(P):
@@ -55,6 +57,16 @@ def test_no_alloc_matches_regular_entry_point_twice(P):
         eu = (np.abs(got["u"] - ref["u"]).max(axis=(1, 2)) / su).max()
         ex = (np.abs(got["xi"] - ref["xi"]).max(axis=(1, 2)) / sx).max()
         assert eu <= REL_TRAJ and ex <= REL_TRAJ, (eu, ex)
+
+
+def test_no_alloc_meets_the_oracle_bars(P):
+    """The no-allocation path against the FP64 oracle itself: trajectories,
+    oracle-checked KKT, objective gap and the device certificate, on both
+    contact models (the active-face bits are not among its outputs)."""
+    for batch, ids in ((W.generate(W.rl_scale_walking(B=24, N=20, seed=2028)), [0, 5, 11, 17, 23]),
+                       (W.generate(W.small_centroidal(B=16, N=10, seed=2029)), [0, 3, 8, 15])):
+        got = _noalloc(P, batch)
+        compare(batch, got, ids, check_bits=False)
 
 
 def test_no_alloc_rejects_batches_beyond_its_scratch(P):
