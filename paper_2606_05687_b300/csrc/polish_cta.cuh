@@ -140,6 +140,29 @@ struct CCtx {
     }
 };
 
+// CTA-wide maxima of several values at once (one pair of barriers); the
+// reduction buffer holds 32 floats, 4 warps x NV values
+template <class D, int NV>
+__device__ void cta_max_n(const CCtx<D>& c, float (&v)[NV]) {
+    static_assert(NV * (kPT / 32) <= 32, "reduction buffer");
+    float* red = c.sm + CtaSmem<D>::ored;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_max(v[i]);
+    __syncthreads();
+    if (c.lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[i * (kPT / 32) + c.warp] = v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float r = red[i * (kPT / 32)];
+#pragma unroll
+        for (int w = 1; w < kPT / 32; ++w) r = fmaxf(r, red[i * (kPT / 32) + w]);
+        v[i] = r;
+    }
+}
+
 template <class D>
 __device__ float cta_max(const CCtx<D>& c, float v) {
     float* red = c.sm + CtaSmem<D>::ored;
@@ -724,8 +747,12 @@ __device__ float cta_certificate(const CCtx<D>& c) {
             uinf = fmaxf(uinf, fabsf(c.ur()[e]) * sig);
         }
     }
-    den = cta_max(c, den);
-    uinf = cta_max(c, uinf);
+    {
+        float m2[2] = {den, uinf};
+        cta_max_n<D, 2>(c, m2);
+        den = m2[0];
+        uinf = m2[1];
+    }
     float feas = 0.0f, stat = 0.0f, comp = 0.0f;
     for (int e = tid; e < c.Nh * D::NC; e += kPT) {
         const int k = e / D::NC, q = e % D::NC;
@@ -813,9 +840,13 @@ __device__ float cta_certificate(const CCtx<D>& c) {
             }
         }
     }
-    feas = cta_max(c, feas);
-    stat = cta_max(c, stat);
-    comp = cta_max(c, comp);
+    {
+        float m3[3] = {feas, stat, comp};
+        cta_max_n<D, 3>(c, m3);
+        feas = m3[0];
+        stat = m3[1];
+        comp = m3[2];
+    }
     // each term |res| / (kc + scale) <= kkt_tol  <=>  |res| <= kkt_tol_abs + kkt_tol scale
     return fmaxf(feas, fmaxf(stat / (c.kc + den), comp / (c.kc + uinf)));
 }
