@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MPC QP solves/s at B=4096 N=20 (KKT≤1e-5); served p50/p99 solve latency"
 B_BENCH, N_BENCH, SEED = 4096, 20, 1002
 INFLIGHT = 3  # batches in flight on separate handles and streams (--inflight)
+E2E_MIN_STEPS = 30  # end-to-end steps timed at least (see the e2e leg)
 SERVE_HANDLES = 4  # handles of the served-latency leg (requests answered as their round ends)
 KKT_TOL = 1e-5
 PLAIN_ITERS = 200  # the paper's iteration budget (plain_admm leg)
@@ -489,7 +490,7 @@ def run_gpu(args):
               "latency_ms": {"p50": float(np.percentile(step1_ms, 50)), "p99": float(np.percentile(step1_ms, 99))},
               "clocks": clk1.summary()}
 
-    e2e_val, h2d, d2h = None, 0, 0
+    e2e_val, h2d, d2h, e2e_steps = None, 0, 0, 0
     if not args.device_only:
         # end to end through the C ABI from pinned host buffers, on the same
         # INFLIGHT handles and streams: the host-to-device copy (and packing)
@@ -521,13 +522,17 @@ def run_gpu(args):
             for sx in streams:
                 sx.synchronize()
 
+        # at least E2E_MIN_STEPS steps: the timed job starts with an empty
+        # pipeline (the first batch's 192 MB copy precedes any solve), and at 10
+        # steps that one-time fill is ~9 % of the job
+        e2e_steps = max(args.steps, E2E_MIN_STEPS)
         e2e_run(args.warmup)
         barrier()
         t0 = time.perf_counter()
-        e2e_run(args.steps)
+        e2e_run(e2e_steps)
         barrier()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        last_o = outs[(args.steps - 1) % INFLIGHT]
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        last_o = outs[(e2e_steps - 1) % INFLIGHT]
         e2e_ok = int(((last_o[2].numpy() == 0) & (last_o[3].numpy() <= KKT_TOL)).sum())
         e2e_s, e2e_ok = job_totals(world, e2e_s, e2e_ok, dev)
         e2e_val = e2e_ok / e2e_s
@@ -836,7 +841,8 @@ def run_gpu(args):
                    "parallelism": f"replicas{world}", "l2": "inputs 192 MB per step > 126 MB L2 (no flush)",
                    "inflight": INFLIGHT,
                    "max_iter": args.max_iter or "library default per shape"},
-        "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        "e2e": ({"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "steps": e2e_steps}
                 if e2e_val is not None else None),
         "single_stream": single,
         "served": served,
