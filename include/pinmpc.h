@@ -152,9 +152,11 @@ typedef struct mpc_stage_view {
     const float* xhi;       /* [B][N][nx]     xlo_k <= xi_{k+1} <= xhi_k (+-INFINITY: unbounded
                                               component); either or both NULL = unbounded.  The
                                               ADMM projects the state part of z onto the box; the
-                                              polish holds the bounds its iterate sits at by an
-                                              augmented Lagrangian, and the certificate includes
-                                              their feasibility and multipliers */
+                                              polish holds the bounds its iterate sits at exactly
+                                              (an equality row of the stage whose inputs move the
+                                              component, up to 4 per stage) or else by an augmented
+                                              Lagrangian, and the certificate includes their
+                                              feasibility and multipliers */
 } mpc_stage_view;
 
 typedef struct mpc_handle mpc_handle;

@@ -224,7 +224,7 @@ struct mpc_handle {
     int optin_smem = 0;          // opt-in shared memory per CTA
     int round_attr = 0;          // dynamic shared memory the round kernel is set up for
     int warm_B = 0, warm_N = 0;  // a warm start is pending for instances [0, warm_B) at horizon stride warm_N
-    float* Kst = nullptr;        // [B_max][N_max][nu][nx+1] polish gains
+    float* Kst = nullptr;        // [B_max][N_max][nu + kNCB][nx+1] polish gains (and bound multiplier gains)
     float* staging = nullptr;  // device copies of host-memory inputs
     // host-input copies run on their own stream: they wait only until the
     // previous pack has read the staging buffer, so they overlap the solve
@@ -403,7 +403,7 @@ static uint64_t workspace_bytes_of(const mpc_config& c, const Shape& sh) {
     const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * nc * sizeof(uint32_t);
-    const size_t kst_b = B * N * nu * (c.nx + 1) * sizeof(float);
+    const size_t kst_b = B * N * (nu + kNCB) * (c.nx + 1) * sizeof(float);  // gains + bound multiplier gains
     const size_t round_b = cache_b + state_b + 2 * modes_b + (2 + 2 * kMaxClasses) * B * sizeof(int) +
                            3 * kMaxClasses * sizeof(int) + kst_b;
     const size_t box_b = B * N * (2 * (size_t)c.nx * sizeof(float) + 2 * sizeof(uint32_t));
@@ -532,7 +532,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_handle** out) {
     const size_t cache_b = B * (size_t)sh.cache_floats(c.N_max) * sizeof(float);
     const size_t state_b = B * (size_t)sh.state_floats(c.N_max) * sizeof(float);
     const size_t modes_b = B * N * h->nc * sizeof(uint32_t);
-    const size_t kst_b = B * N * h->nu * (c.nx + 1) * sizeof(float);
+    const size_t kst_b = B * N * (h->nu + kNCB) * (c.nx + 1) * sizeof(float);  // gains + bound multiplier gains
     h->bytes = workspace_bytes_of(c, sh);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) { cudaGetLastError(); free_b = (size_t)-1; }

@@ -46,7 +46,7 @@ struct RoundArgs {
     int* cursor;             // [2] work cursors of the round and polish kernels, zeroed per round
     int warm_B;              // instances b < warm_B start round 0 from the stored (shifted) iterate
     int dbl;                 // round kernel: records and factors arrive by TMA into two alternating buffers
-    float* Kst;              // [B][N][NU][NX+1] polish gains
+    float* Kst;              // [B][N][NU + kNCB][NX+1] polish gains (and bound multiplier gains)
     float* out_xi;
     float* out_u;
     int* out_status;
@@ -82,6 +82,12 @@ constexpr float kBoxRate = 0.1f;
 constexpr float kBoxPenaltyMax = 1e7f;
 constexpr int kBoxIters = 12;
 constexpr float kBoxViol = 1e-7f;
+// At most this many active state bounds per stage are held exactly in the
+// polish (those whose component the stage's free inputs move directly: an
+// equality row added to the stage's KKT system); the others, and bounds on
+// components no free input of the stage reaches, go through the augmented
+// Lagrangian above.
+constexpr int kNCB = 4;
 
 // Class of an instance with horizon Nh: the first class whose cap holds it;
 // a horizon outside [1, N] goes to the last class (cap N), whose round kernel

@@ -48,17 +48,23 @@ struct CtaSmem {
                          osv = al(oet + XP), odv = al(osv + XP), oSBT = al(odv + XP), oSAT = al(oSBT + NU * XP),
                          oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
                          oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oMC = al(ofree + 4),
-                         opcb = al(oMC + (NU + NK) * 32), oScanEnd = al(opcb + 2 * kPivotBlock * 32),
+                         opcb = al(oMC + (NU + kNCB + NK) * 32),
+                         // exact state bounds of the stage (state-box variant): multiplier gains
+                         // [K_lambda | kappa_lambda] per slot, and each slot's component and bound
+                         oKl = al(opcb + 2 * kPivotBlock * 32), oslot = al(oKl + kNCB * XP),
+                         oScanEnd = al(oslot + 2 * kNCB),
                          // forward rollout and certificate
-                         oK = oScanEnd, out = al(oK + NU * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
+                         oK = oScanEnd, out = al(oK + (NU + kNCB) * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
                          ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
     static_assert(NU + NK <= 48, "pivot-row buffer");
     // column stride of the column-major [M | RHS]: a multiple of 4 at least NU
     // with an odd number of float4s, so consecutive columns read as float4
     // fall in different bank quads
-    static constexpr int CP = (((NU + 3) / 4) % 2 == 1) ? 4 * ((NU + 3) / 4) : 4 * ((NU + 3) / 4) + 4;
+    // (with room for the kNCB rows of exactly held state bounds)
+    static constexpr int NRB = NU + kNCB;
+    static constexpr int CP = (((NRB + 3) / 4) % 2 == 1) ? 4 * ((NRB + 3) / 4) : 4 * ((NRB + 3) / 4) + 4;
     static_assert(CP <= 32, "column buffer");
-    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, total;
+    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, dbits, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
@@ -76,6 +82,7 @@ struct CtaSmem {
         rhob = take(N * NX);  // their augmented-Lagrangian penalties
         dprev = take(N * NX); // their violations after the previous scan
         sbits = take(N);      // active state bounds per stage (bit i lower, 16 + i upper)
+        dbits = take(N);      // of those, the components held exactly by the last scan (bit i)
         total = o;
     }
 };
@@ -129,6 +136,7 @@ struct CCtx {
     __device__ float* rhob() const { return sm + L.rhob; }
     __device__ float* dprev() const { return sm + L.dprev; }
     __device__ uint32_t* sbits() const { return reinterpret_cast<uint32_t*>(sm + L.sbits); }
+    __device__ uint32_t* dbits() const { return reinterpret_cast<uint32_t*>(sm + L.dbits); }
     // the bound of component i of xi_{k+1} that is active (upper if both), and whether any is
     __device__ bool box_active(int k, int i, float* bound, bool* upper) const {
         const uint32_t sb = sbits()[k];
@@ -235,6 +243,12 @@ __device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((
 // M is kept at full size: an eliminated column makes row and column of M a
 // unit vector and its row of the right-hand side zero, so its elimination
 // step is skipped and its gains come out zero.
+// With state bounds (BOX), an active bound b_i on component i of xi_{k+1}
+// whose row Bt_i is nonzero is an equality row of the stage's system,
+//   [M  Bt_I'] [ut    ]   [-Bt'S A | Bt'(s - S et) - gt]
+//   [Bt_I  0 ] [lambda] = [ -A_I   | b_I - et_I       ]  [x; 1],
+// lambda = K_lambda x + kappa_lambda its multiplier (L = f + lambda'(x_I - b_I)),
+// and then G += E_I'K_lambda, g2 -= E_I'kappa_lambda (E_I selects rows I).
 template <class D, bool BOX = false>
 __device__ int cta_polish(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
@@ -269,22 +283,9 @@ __device__ int cta_polish(const CCtx<D>& c) {
         pf.store(s, tid);
         __syncthreads();
         if (k > 0) pf.load(c.grec(k - 1), tid);
-        if constexpr (BOX) {
-            // augmented Lagrangian of the active state bounds: the stage cost of
-            // component i gains p_i/2 (x_i - b_i + nu_i / p_i)^2 (p_i its penalty),
-            // i.e. Q_i + p_i and Q_i r_i + p_i b_i - nu_i
-            float bnd;
-            bool up;
-            if (tid < NX && c.box_active(k, tid, &bnd, &up)) {
-                const float q = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
-                const float qn = q + pen;
-                s[D::oRY + tid] = (fmaf(q, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
-                s[D::oQ + tid] = qn;
-            }
-            __syncthreads();
-        }
         // (1) warp 0: reduced input map (one column per lane), free columns, et.
-        //     warps 1..3: S = Q + sym(P), s = Q ry + p, AT = A'
+        //     warps 1..3: S = Q + sym(P), s = Q ry + p, AT = A' (with state
+        //     bounds: AT only, S and s once the bounds' cost terms are set)
         if (tid < 32) {
             bool fr = false;
             if (tid < NU) {
@@ -316,11 +317,16 @@ __device__ int cta_polish(const CCtx<D>& c) {
         } else {
             for (int e = tid - 32; e < NX * XP + NX + NX * NX; e += kPT - 32) {
                 if (e < NX * XP) {
-                    const int r = e / XP, cc = e % XP;
-                    S[e] = cc < NX ? 0.5f * (Xp[r * XP + cc] + Xp[cc * XP + r]) + (r == cc ? s[D::oQ + r] : 0.0f) : 0.0f;
+                    if (!BOX) {
+                        const int r = e / XP, cc = e % XP;
+                        S[e] = cc < NX ? 0.5f * (Xp[r * XP + cc] + Xp[cc * XP + r]) + (r == cc ? s[D::oQ + r] : 0.0f)
+                                       : 0.0f;
+                    }
                 } else if (e < NX * XP + NX) {
-                    const int r = e - NX * XP;
-                    sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], Xp[r * XP + NX]);
+                    if (!BOX) {
+                        const int r = e - NX * XP;
+                        sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], Xp[r * XP + NX]);
+                    }
                 } else {
                     const int f = e - NX * XP - NX, i = f / NX, cc = f % NX;
                     AT[cc * XP + i] = s[D::oA + f];
@@ -328,6 +334,53 @@ __device__ int cta_polish(const CCtx<D>& c) {
             }
         }
         __syncthreads();
+        uint32_t cmask = 0u;  // constraint slots in use
+        if constexpr (BOX) {
+            // Active state bounds.  A component that the stage's free inputs
+            // move (a nonzero row i of Bt) is held exactly: an equality row
+            // Bt_i ut = b_i - A_i x - et_i in the stage's KKT system (at most
+            // kNCB, in component order).  The others get the augmented
+            // Lagrangian's terms in the stage cost, p_i/2 (x_i - b_i + nu_i /
+            // p_i)^2 (p_i its penalty), i.e. Q_i + p_i and Q_i r_i + p_i b_i - nu_i.
+            int* slot_i = reinterpret_cast<int*>(sm + CS::oslot);
+            float* slot_b = sm + CS::oslot + kNCB;
+            if (tid < 32) {
+                float bnd = 0.0f;
+                bool up = false;
+                const bool act = tid < NX && c.box_active(k, tid, &bnd, &up);
+                bool dir = false;
+                if (act)
+                    for (int a = 0; a < NU; ++a) dir |= BtT[a * XP + tid] != 0.0f;
+                const unsigned d0 = __ballot_sync(0xffffffffu, act && dir);
+                dir = dir && __popc(d0 & ((1u << tid) - 1u)) < kNCB;
+                const unsigned dm = __ballot_sync(0xffffffffu, act && dir);
+                if (act && dir) {
+                    const int t = __popc(dm & ((1u << tid) - 1u));
+                    slot_i[t] = tid;
+                    slot_b[t] = bnd;
+                }
+                if (tid >= __popc(dm) && tid < kNCB) slot_i[tid] = -1;
+                if (act && !dir) {
+                    const float q = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
+                    const float qn = q + pen;
+                    s[D::oRY + tid] = (fmaf(q, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
+                    s[D::oQ + tid] = qn;
+                }
+                if (tid == 0) c.dbits()[k] = dm;
+            }
+            __syncthreads();
+            for (int e = tid; e < NX * XP + NX; e += kPT) {
+                if (e < NX * XP) {
+                    const int r = e / XP, cc = e % XP;
+                    S[e] = cc < NX ? 0.5f * (Xp[r * XP + cc] + Xp[cc * XP + r]) + (r == cc ? s[D::oQ + r] : 0.0f) : 0.0f;
+                } else {
+                    const int r = e - NX * XP;
+                    sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], Xp[r * XP + NX]);
+                }
+            }
+            cmask = (1u << __popc(c.dbits()[k])) - 1u;
+            __syncthreads();
+        }
         const uint32_t fmask = freep[0];
         npiv += __popc(fmask);
         // (2) SBT = (S Bt)', SAT = (S A)', Se: thread (column, row group) with
@@ -376,16 +429,42 @@ __device__ int cta_polish(const CCtx<D>& c) {
                     }
                     m[t] = acc;
                 }
+                // with state bounds the right-hand sides follow the kNCB bound columns
+                const int jm = (BOX && j >= NU) ? j + kNCB : j;
                 if constexpr (RG % 4 == 0 && (NU % RG) == 0) {
 #pragma unroll
                     for (int q = 0; q < RG / 4; ++q)
-                        reinterpret_cast<float4*>(MC + j * CP + g * RG)[q] =
+                        reinterpret_cast<float4*>(MC + jm * CP + g * RG)[q] =
                             make_float4(m[4 * q], m[4 * q + 1], m[4 * q + 2], m[4 * q + 3]);
                 } else {
 #pragma unroll
                     for (int t = 0; t < RG; ++t)
-                        if (g * RG + t < NU) MC[j * CP + g * RG + t] = m[t];
+                        if (g * RG + t < NU) MC[jm * CP + g * RG + t] = m[t];
                 }
+            }
+        }
+        if constexpr (BOX) {
+            // the bound rows NU + t of [M | RHS]: [Bt_i | 0 | -A_i | b_i - et_i],
+            // and the bound columns NU + t: Bt_i' (a unit pivot for a free slot)
+            const int* slot_i = reinterpret_cast<const int*>(sm + CS::oslot);
+            const float* slot_b = sm + CS::oslot + kNCB;
+            constexpr int NR = NU + kNCB, WB = NR + NK;
+            for (int e = tid; e < kNCB * WB; e += kPT) {
+                const int t = e / WB, col = e % WB, i = slot_i[t];
+                float v = 0.0f;
+                if (i < 0) {
+                    v = (col == NU + t) ? 1.0f : 0.0f;
+                } else if (col < NU) {
+                    v = BtT[col * XP + i];
+                } else if (col >= NR) {
+                    const int cc = col - NR;
+                    v = cc < NX ? -s[D::oA + i * NX + cc] : slot_b[t] - et[i];
+                }
+                MC[col * CP + NU + t] = v;
+            }
+            for (int e = tid; e < kNCB * NU; e += kPT) {
+                const int t = e / NU, a = e % NU, i = slot_i[t];
+                MC[(NU + t) * CP + a] = i < 0 ? 0.0f : BtT[a * XP + i];
             }
         }
         __syncthreads();
@@ -410,15 +489,19 @@ __device__ int cta_polish(const CCtx<D>& c) {
         const int gj = tid - ((blockIdx.x & 1) ? 64 : 0);  // column index in the eliminating warps
         if (gj >= 0 && gj < 64) {
             constexpr int PB = kPivotBlock;
-            static_assert(W <= 64, "elimination runs on two warps");
-            static_assert(NU % PB == 0, "pivot blocks tile the inputs");
+            // rows: the inputs, then (with state bounds) the kNCB bound rows
+            constexpr int NR = BOX ? NU + kNCB : NU, WR = NR + NK;
+            static_assert(WR <= 64, "elimination runs on two warps");
+            static_assert(NU % PB == 0 && kNCB % PB == 0, "pivot blocks tile the rows");
+            static_assert(NR <= CP, "column buffer");
             float* pcb = sm + CS::opcb;
-            const bool act = gj < W;
+            const bool act = gj < WR;
+            const uint32_t pmask = fmask | (cmask << NU);
             // rows held in rotated order: before block pq, register 4 t + i
-            // holds row 4 (pq + t) + i (mod NU), so the block's pivot rows are
+            // holds row 4 (pq + t) + i (mod NR), so the block's pivot rows are
             // always registers 0..3 and the block loop need not be unrolled
-            constexpr int NQ = NU / PB;
-            float xc[NU];
+            constexpr int NQ = NR / PB;
+            float xc[NR];
             {
                 const float4* c4 = reinterpret_cast<const float4*>(MC + (act ? gj : 0) * CP);
 #pragma unroll
@@ -434,7 +517,7 @@ __device__ int cta_polish(const CCtx<D>& c) {
 #pragma unroll 1
             for (int pq = 0; pq < NQ; ++pq) {
                 const int p0 = PB * pq;
-                if ((fmask >> p0) & ((1u << PB) - 1u)) {
+                if ((pmask >> p0) & ((1u << PB) - 1u)) {
                     float* buf = pcb + bsel * (PB * 32);
                     if (gj >= p0 && gj < p0 + PB) {
                         float4* dst = reinterpret_cast<float4*>(buf + (gj - p0) * 32);
@@ -490,26 +573,36 @@ __device__ int cta_polish(const CCtx<D>& c) {
                 // rotate by one block: registers 0..3 move to the end
                 float t0 = xc[0], t1 = xc[1], t2 = xc[2], t3 = xc[3];
 #pragma unroll
-                for (int i = 0; i < NU - PB; ++i) xc[i] = xc[i + PB];
-                xc[NU - 4] = t0;
-                xc[NU - 3] = t1;
-                xc[NU - 2] = t2;
-                xc[NU - 1] = t3;
+                for (int i = 0; i < NR - PB; ++i) xc[i] = xc[i + PB];
+                xc[NR - 4] = t0;
+                xc[NR - 3] = t1;
+                xc[NR - 2] = t2;
+                xc[NR - 1] = t3;
             }
-            // (5) gains to K16 (scan) and to global memory (rollout)
-            if (act && gj >= NU) {
-                float* Kg = c.K + (size_t)k * NU * NK;
-                const int cc = gj - NU;
+            // (5) gains to K16 (scan) and to global memory (rollout); with state
+            // bounds also the bounds' multiplier gains (rows NU + t)
+            if (act && gj >= NR) {
+                float* Kg = c.K + (size_t)k * NR * NK;
+                const int cc = gj - NR;
 #pragma unroll
                 for (int a = 0; a < NU; ++a) {
                     K16[a * XP + cc] = xc[a];
                     Kg[a * NK + cc] = xc[a];
                 }
+                if constexpr (BOX) {
+                    float* Kl = sm + CS::oKl;
+#pragma unroll
+                    for (int t = 0; t < kNCB; ++t) {
+                        Kl[t * XP + cc] = xc[NU + t];
+                        Kg[(NU + t) * NK + cc] = xc[NU + t];
+                    }
+                }
             }
         }
         __syncthreads();
-        // (6) GR = [G | g2]: G = SA + SB K, g2 = dv - SB kappa; thread (row r,
-        //     column quad cq, half h of the inputs), halves combined by a shuffle
+        // (6) GR = [G | g2]: G = SA + SB K (+ E'K_lambda for exactly held bounds),
+        //     g2 = dv - SB kappa (- E'kappa_lambda); thread (row r, column quad
+        //     cq, half h of the inputs), halves combined by a shuffle
         {
             const int h = tid & 1, cq = (tid >> 1) & 3, r = tid >> 3;
             float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -537,6 +630,22 @@ __device__ int cta_polish(const CCtx<D>& c) {
                 for (int q = 0; q < 4; ++q) {
                     const int cc = 4 * cq + q;
                     o[q] = cc < NX ? SAT[cc * XP + r] + o[q] : (cc == NX ? dv[r] - o[q] : 0.0f);
+                }
+                if constexpr (BOX) {
+                    // a bound held exactly on component r: G_r += K_lambda, g2_r -= kappa_lambda
+                    const int* slot_i = reinterpret_cast<const int*>(sm + CS::oslot);
+                    const float* Kl = sm + CS::oKl;
+#pragma unroll
+                    for (int t = 0; t < kNCB; ++t) {
+                        if (slot_i[t] == r) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const int cc = 4 * cq + q;
+                                if (cc < NX) o[q] += Kl[t * XP + cc];
+                                else if (cc == NX) o[q] -= Kl[t * XP + NX];
+                            }
+                        }
+                    }
                 }
                 reinterpret_cast<float4*>(GR + r * XP)[cq] = make_float4(o[0], o[1], o[2], o[3]);
             }
@@ -569,7 +678,8 @@ __device__ int cta_polish(const CCtx<D>& c) {
     }
     // forward rollout: ut = K x + kappa, u = T ut + o, x' = A x + Bs u + e
     float* ut = sm + CS::out;
-    CPrefetch<NU * NK, false> pk;
+    constexpr int NRK = (BOX ? NU + kNCB : NU) * NK;  // gains per stage
+    CPrefetch<NRK, false> pk;
     __syncthreads();
     pf.load(c.grec(0), tid);
     pk.load(c.K, tid);
@@ -581,7 +691,7 @@ __device__ int cta_polish(const CCtx<D>& c) {
         __syncthreads();
         if (k + 1 < c.Nh) {
             pf.load(c.grec(k + 1), tid);
-            pk.load(c.K + (size_t)(k + 1) * NU * NK, tid);
+            pk.load(c.K + (size_t)(k + 1) * NRK, tid);
         }
         const float* xk = c.xr() + k * NX;
         if (tid < NU) {
@@ -589,6 +699,19 @@ __device__ int cta_polish(const CCtx<D>& c) {
 #pragma unroll
             for (int r = 0; r < NX; ++r) acc = fmaf(Ks[tid * NK + r], xk[r], acc);
             ut[tid] = acc;
+        } else if (BOX && tid < NU + kNCB) {
+            // the multiplier of the exactly held bound in slot t (its component
+            // the t-th set bit of the stage's dbits), lambda = K_lambda x + kappa_lambda
+            const int t = tid - NU;
+            uint32_t dm = c.dbits()[k];
+            if (t < __popc(dm)) {
+                for (int q = 0; q < t; ++q) dm &= dm - 1u;
+                const int i = __ffs(dm) - 1;
+                float acc = Ks[(NU + t) * NK + NX];
+#pragma unroll
+                for (int r = 0; r < NX; ++r) acc = fmaf(Ks[(NU + t) * NK + r], xk[r], acc);
+                c.nub()[k * NX + i] = acc;
+            }
         }
         __syncthreads();
         if (tid < D::NC) {
@@ -659,12 +782,12 @@ __device__ void cta_box_init(const CCtx<D>& c, const RoundArgs& a, int b) {
     __syncthreads();
 }
 
-// Polish with the active state bounds held by an augmented Lagrangian: scans
-// with the penalised stage costs (see cta_polish), each followed by the
-// multiplier step nu += kBoxPenalty (x - b) on the active bounds, until every
-// active bound holds to kBoxViol (relative) or kBoxIters scans.  Without
-// active bounds this is one plain scan.  Returns the pivots eliminated and
-// adds the scans to *nscan.
+// Polish with active state bounds: scans (see cta_polish, which holds a
+// bound exactly when the stage's free inputs move its component), each
+// followed by the multiplier step nu += p (x - b) on the bounds held by the
+// augmented Lagrangian instead, until every active bound holds to kBoxViol
+// (relative) or kBoxIters scans.  Without active bounds this is one plain
+// scan.  Returns the pivots eliminated and adds the scans to *nscan.
 template <class D, bool BOX>
 __device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
     constexpr int NX = D::NX;
@@ -685,12 +808,17 @@ __device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
             bool up;
             if (c.box_active(k, i, &bnd, &up)) {
                 const float d = c.xr()[(k + 1) * NX + i] - bnd;
-                const float pen = c.rhob()[e];
-                c.nub()[e] = fmaf(pen, d, c.nub()[e]);
                 const float vi = fabsf(d) / (1.0f + fabsf(bnd));
-                // a stiff bound (its violation falls too slowly) gets a larger penalty
-                if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e]) c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
-                c.dprev()[e] = fabsf(d);
+                if (!((c.dbits()[k] >> i) & 1u)) {
+                    // held by the augmented Lagrangian (an exactly held bound
+                    // has its multiplier from the scan)
+                    const float pen = c.rhob()[e];
+                    c.nub()[e] = fmaf(pen, d, c.nub()[e]);
+                    // a stiff bound (its violation falls too slowly) gets a larger penalty
+                    if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e])
+                        c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
+                    c.dprev()[e] = fabsf(d);
+                }
                 viol = fmaxf(viol, vi);
             }
         }
@@ -958,7 +1086,7 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
     c.sm = psm;
     c.rec = a.rec + (size_t)b * a.irec;
     c.modes = reinterpret_cast<uint32_t*>(c.sm + c.L.modes);
-    c.K = a.Kst + (size_t)b * a.N * NU * (NX + 1);
+    c.K = a.Kst + (size_t)b * a.N * (NU + kNCB) * (NX + 1);  // [N][NU (+ kNCB)][NX + 1]
     c.tid = threadIdx.x;
     c.lane = threadIdx.x & 31;
     c.warp = threadIdx.x >> 5;
