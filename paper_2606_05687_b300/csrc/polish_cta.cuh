@@ -345,25 +345,54 @@ __device__ int cta_polish(const CCtx<D>& c) {
             int* slot_i = reinterpret_cast<int*>(sm + CS::oslot);
             float* slot_b = sm + CS::oslot + kNCB;
             if (tid < 32) {
-                float bnd = 0.0f;
-                bool up = false;
-                const bool act = tid < NX && c.box_active(k, tid, &bnd, &up);
-                bool dir = false;
-                if (act)
-                    for (int a = 0; a < NU; ++a) dir |= BtT[a * XP + tid] != 0.0f;
-                const unsigned d0 = __ballot_sync(0xffffffffu, act && dir);
-                dir = dir && __popc(d0 & ((1u << tid) - 1u)) < kNCB;
-                const unsigned dm = __ballot_sync(0xffffffffu, act && dir);
-                if (act && dir) {
-                    const int t = __popc(dm & ((1u << tid) - 1u));
-                    slot_i[t] = tid;
-                    slot_b[t] = bnd;
+                // candidates in component order; a bound's row Bt_i (lane a holds
+                // entry a) is kept when it adds rank to the rows kept before it
+                // (Gram-Schmidt residual above 1e-6 of its norm), so the bound
+                // rows stay independent and the system nonsingular
+                float q[kNCB];
+                int nd = 0;
+                uint32_t dm = 0u, am = 0u;
+                for (int i = 0; i < NX; ++i) {
+                    float bnd;
+                    bool up;
+                    if (!c.box_active(k, i, &bnd, &up)) continue;  // uniform: every lane reads the same bits
+                    float v = tid < NU ? BtT[tid * XP + i] : 0.0f;
+                    const float n2 = warp_sum(v * v);
+                    bool keep = n2 > 0.0f && nd < kNCB;
+                    if (keep) {
+#pragma unroll
+                        for (int t = 0; t < kNCB; ++t) {
+                            if (t < nd) {
+                                const float pr = warp_sum(v * q[t]);
+                                v = fmaf(-pr, q[t], v);
+                            }
+                        }
+                        const float r2 = warp_sum(v * v);
+                        keep = r2 > 1e-6f * n2;
+                        if (keep) {
+                            const float inv = rsqrtf(r2);
+#pragma unroll
+                            for (int t = 0; t < kNCB; ++t)
+                                if (t == nd) q[t] = v * inv;
+                            if (tid == 0) {
+                                slot_i[nd] = i;
+                                slot_b[nd] = bnd;
+                            }
+                            ++nd;
+                            dm |= 1u << i;
+                        }
+                    }
+                    if (!keep) am |= 1u << i;
                 }
-                if (tid >= __popc(dm) && tid < kNCB) slot_i[tid] = -1;
-                if (act && !dir) {
-                    const float q = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
-                    const float qn = q + pen;
-                    s[D::oRY + tid] = (fmaf(q, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
+                if (tid >= nd && tid < kNCB) slot_i[tid] = -1;
+                // the others: augmented-Lagrangian terms in the stage cost
+                if (tid < NX && ((am >> tid) & 1u)) {
+                    float bnd;
+                    bool up;
+                    c.box_active(k, tid, &bnd, &up);
+                    const float qq = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
+                    const float qn = qq + pen;
+                    s[D::oRY + tid] = (fmaf(qq, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
                     s[D::oQ + tid] = qn;
                 }
                 if (tid == 0) c.dbits()[k] = dm;
