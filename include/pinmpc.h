@@ -153,10 +153,10 @@ typedef struct mpc_stage_view {
                                               component); either or both NULL = unbounded.  The
                                               ADMM projects the state part of z onto the box; the
                                               polish holds the bounds its iterate sits at exactly
-                                              (an equality row of the stage whose inputs move the
-                                              component, up to 4 per stage) or else by an augmented
-                                              Lagrangian, and the certificate includes their
-                                              feasibility and multipliers */
+                                              (an equality row of the first stage, at or before the
+                                              bound's, whose inputs move the component; up to 4 per
+                                              stage) or else by an augmented Lagrangian, and the
+                                              certificate includes their feasibility and multipliers */
 } mpc_stage_view;
 
 typedef struct mpc_handle mpc_handle;

@@ -83,11 +83,14 @@ constexpr float kBoxPenaltyMax = 1e7f;
 constexpr int kBoxIters = 12;
 constexpr float kBoxViol = 1e-7f;
 // At most this many active state bounds per stage are held exactly in the
-// polish (those whose component the stage's free inputs move directly: an
-// equality row added to the stage's KKT system); the others, and bounds on
-// components no free input of the stage reaches, go through the augmented
+// polish (an equality row added to the KKT system of a stage whose free
+// inputs move the bounded quantity); the others go through the augmented
 // Lagrangian above.
 constexpr int kNCB = 4;
+// A bound on a component no free input of its stage moves (a position behind
+// a velocity) is carried back, as a row F on an earlier stage's state, to the
+// first stage whose inputs reach it; at most this many are carried at once.
+constexpr int kNPend = 8;
 
 // Class of an instance with horizon Nh: the first class whose cap holds it;
 // a horizon outside [1, N] goes to the last class (cap N), whose round kernel

@@ -49,10 +49,16 @@ struct CtaSmem {
                          oK16 = al(oSAT + NX * XP), oGR = al(oK16 + NU * XP), opcol = al(oGR + NX * XP),
                          oprow = al(opcol + 128), ofree = al(oprow + 4 * 48), oMC = al(ofree + 4),
                          opcb = al(oMC + (NU + kNCB + NK) * 32),
-                         // exact state bounds of the stage (state-box variant): multiplier gains
-                         // [K_lambda | kappa_lambda] per slot, and each slot's component and bound
-                         oKl = al(opcb + 2 * kPivotBlock * 32), oslot = al(oKl + kNCB * XP),
-                         oScanEnd = al(oslot + 2 * kNCB),
+                         // exactly held state bounds (state-box variant): per slot of the stage the
+                         // multiplier gains [K_lambda | kappa_lambda], the row F on x_{k+1}, its
+                         // input row F Bt, feedback row -F A and affine term d - F et; the rows
+                         // carried back to earlier stages (two lists, read and written in turn),
+                         // with their bound and origin (stage * NX + component)
+                         oKl = al(opcb + 2 * kPivotBlock * 32), osF = al(oKl + kNCB * XP),
+                         osc = al(osF + kNCB * XP), osfb = al(osc + kNCB * 32), osaff = al(osfb + kNCB * XP),
+                         opF = al(osaff + 2 * kNCB), opd = al(opF + 2 * kNPend * XP),
+                         opo = al(opd + 2 * kNPend), opn = al(opo + 2 * kNPend),
+                         oScanEnd = al(opn + 4),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + (NU + kNCB) * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
                          ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
@@ -64,7 +70,7 @@ struct CtaSmem {
     static constexpr int NRB = NU + kNCB;
     static constexpr int CP = (((NRB + 3) / 4) % 2 == 1) ? 4 * ((NRB + 3) / 4) : 4 * ((NRB + 3) / 4) + 4;
     static_assert(CP <= 32, "column buffer");
-    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, dbits, total;
+    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, dbits, albits, sorig, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
@@ -83,6 +89,8 @@ struct CtaSmem {
         dprev = take(N * NX); // their violations after the previous scan
         sbits = take(N);      // active state bounds per stage (bit i lower, 16 + i upper)
         dbits = take(N);      // of those, the components held exactly by the last scan (bit i)
+        albits = take(N);     // and those left to the augmented Lagrangian by this polish
+        sorig = take(N * kNCB);  // origin (stage * NX + component) of each stage's exact rows, -1 if none
         total = o;
     }
 };
@@ -137,6 +145,8 @@ struct CCtx {
     __device__ float* dprev() const { return sm + L.dprev; }
     __device__ uint32_t* sbits() const { return reinterpret_cast<uint32_t*>(sm + L.sbits); }
     __device__ uint32_t* dbits() const { return reinterpret_cast<uint32_t*>(sm + L.dbits); }
+    __device__ uint32_t* albits() const { return reinterpret_cast<uint32_t*>(sm + L.albits); }
+    __device__ int* sorig() const { return reinterpret_cast<int*>(sm + L.sorig); }
     // the bound of component i of xi_{k+1} that is active (upper if both), and whether any is
     __device__ bool box_active(int k, int i, float* bound, bool* upper) const {
         const uint32_t sb = sbits()[k];
@@ -336,66 +346,146 @@ __device__ int cta_polish(const CCtx<D>& c) {
         __syncthreads();
         uint32_t cmask = 0u;  // constraint slots in use
         if constexpr (BOX) {
-            // Active state bounds.  A component that the stage's free inputs
-            // move (a nonzero row i of Bt) is held exactly: an equality row
-            // Bt_i ut = b_i - A_i x - et_i in the stage's KKT system (at most
-            // kNCB, in component order).  The others get the augmented
-            // Lagrangian's terms in the stage cost, p_i/2 (x_i - b_i + nu_i /
-            // p_i)^2 (p_i its penalty), i.e. Q_i + p_i and Q_i r_i + p_i b_i - nu_i.
-            int* slot_i = reinterpret_cast<int*>(sm + CS::oslot);
-            float* slot_b = sm + CS::oslot + kNCB;
+            // Active state bounds.  A bound b_i on component i of xi_{k+1} is
+            // the row F = e_i on x_{k+1} = F (A x + Bt ut + et), held exactly
+            // by this stage when F Bt is nonzero: an equality row F Bt ut =
+            // d - F A x - F et of the stage's KKT system.  When F Bt = 0 (no
+            // free input of the stage moves it) the row is carried back as
+            // F A on x_k, d - F et, to the next stage, and so on until a
+            // stage's inputs reach it.  Rows are taken in turn (carried rows,
+            // then the stage's own bounds in component order) while they add
+            // rank (Gram-Schmidt residual above 1e-6 of the norm), up to kNCB;
+            // a bound not held exactly gets the augmented Lagrangian's terms
+            // in its stage cost, p_i/2 (x_i - b_i + nu_i / p_i)^2, i.e.
+            // Q_i + p_i and Q_i r_i + p_i b_i - nu_i (now, or from the next
+            // scan when it was carried).
+            float* sF = sm + CS::osF;
+            float* sc = sm + CS::osc;
+            float* sfb = sm + CS::osfb;
+            float* saff = sm + CS::osaff;
+            int* pn = reinterpret_cast<int*>(sm + CS::opn);
+            const int rd = k & 1;  // the list read at this stage; the other is written
+            float* pFr = sm + CS::opF + rd * kNPend * XP;
+            float* pFw = sm + CS::opF + (1 - rd) * kNPend * XP;
+            float* pdr = sm + CS::opd + rd * kNPend;
+            float* pdw = sm + CS::opd + (1 - rd) * kNPend;
+            int* por = reinterpret_cast<int*>(sm + CS::opo) + rd * kNPend;
+            int* pow_ = reinterpret_cast<int*>(sm + CS::opo) + (1 - rd) * kNPend;
             if (tid < 32) {
-                // candidates in component order; a bound's row Bt_i (lane a holds
-                // entry a) is kept when it adds rank to the rows kept before it
-                // (Gram-Schmidt residual above 1e-6 of its norm), so the bound
-                // rows stay independent and the system nonsingular
+                const int lane = tid;
+                if (lane == 0) c.dbits()[k] = 0u;
+                if (lane < kNCB) c.sorig()[k * kNCB + lane] = -1;
+                __syncwarp();
                 float q[kNCB];
-                int nd = 0;
-                uint32_t dm = 0u, am = 0u;
-                for (int i = 0; i < NX; ++i) {
-                    float bnd;
-                    bool up;
-                    if (!c.box_active(k, i, &bnd, &up)) continue;  // uniform: every lane reads the same bits
-                    float v = tid < NU ? BtT[tid * XP + i] : 0.0f;
+                int nd = 0, nw = 0;
+                uint32_t alm = 0u;  // the stage's own bounds held by the augmented Lagrangian
+                const int nr = (k + 1 < c.Nh) ? pn[rd] : 0;
+                const uint32_t al_k = c.albits()[k];
+                // state rows the stage's inputs act on (nonzero rows of B)
+                bool brow = false;
+                if (lane < NX)
+                    for (int a = 0; a < NU; ++a) brow |= s[D::oB + lane * NU + a] != 0.0f;
+                const uint32_t bmask = __ballot_sync(0xffffffffu, brow);
+                for (int e = 0; e < nr + NX; ++e) {
+                    // candidate row F (lane r < NX holds F_r), bound d, origin
+                    float Fr, d;
+                    int org;
+                    if (e < nr) {
+                        Fr = lane < NX ? pFr[e * XP + lane] : 0.0f;
+                        d = pdr[e];
+                        org = por[e];
+                    } else {
+                        const int i = e - nr;
+                        float bnd;
+                        bool up;
+                        if (!c.box_active(k, i, &bnd, &up)) continue;  // uniform
+                        if ((al_k >> i) & 1u) {
+                            alm |= 1u << i;
+                            continue;
+                        }
+                        Fr = lane == i ? 1.0f : 0.0f;
+                        d = bnd;
+                        org = k * NX + i;
+                    }
+                    // its input row F Bt (lane a: F against Bt's column a)
+                    float v = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < NX; ++r) {
+                        const float fr = __shfl_sync(0xffffffffu, Fr, r);
+                        if (lane < NU) v = fmaf(fr, BtT[lane * XP + r], v);
+                    }
                     const float n2 = warp_sum(v * v);
-                    bool keep = n2 > 0.0f && nd < kNCB;
-                    if (keep) {
+                    bool keep = false;
+                    if (n2 > 0.0f && nd < kNCB) {
+                        float w = v;
 #pragma unroll
                         for (int t = 0; t < kNCB; ++t) {
                             if (t < nd) {
-                                const float pr = warp_sum(v * q[t]);
-                                v = fmaf(-pr, q[t], v);
+                                const float pr = warp_sum(w * q[t]);
+                                w = fmaf(-pr, q[t], w);
                             }
                         }
-                        const float r2 = warp_sum(v * v);
+                        const float r2 = warp_sum(w * w);
                         keep = r2 > 1e-6f * n2;
                         if (keep) {
                             const float inv = rsqrtf(r2);
 #pragma unroll
                             for (int t = 0; t < kNCB; ++t)
-                                if (t == nd) q[t] = v * inv;
-                            if (tid == 0) {
-                                slot_i[nd] = i;
-                                slot_b[nd] = bnd;
-                            }
-                            ++nd;
-                            dm |= 1u << i;
+                                if (t == nd) q[t] = w * inv;
                         }
                     }
-                    if (!keep) am |= 1u << i;
+                    // F A and F et (lane cc < NX: column cc of F A)
+                    float fa = 0.0f, fe = 0.0f;
+#pragma unroll
+                    for (int r = 0; r < NX; ++r) {
+                        const float fr = __shfl_sync(0xffffffffu, Fr, r);
+                        if (lane < NX) fa = fmaf(fr, s[D::oA + r * NX + lane], fa);
+                        fe = fmaf(fr, et[r], fe);
+                    }
+                    if (keep) {
+                        if (lane < NX) {
+                            sF[nd * XP + lane] = Fr;
+                            sfb[nd * XP + lane] = -fa;
+                        }
+                        if (lane < NU) sc[nd * 32 + lane] = v;
+                        if (lane == 0) {
+                            saff[nd] = d - fe;
+                            c.sorig()[k * kNCB + nd] = org;
+                            c.dbits()[org / NX] |= 1u << (org % NX);
+                        }
+                        ++nd;
+                    } else if (n2 == 0.0f && k > 0 && nw < kNPend &&
+                               warp_sum(lane < NX && ((bmask >> lane) & 1u) ? fa * fa : 0.0f) >=
+                                   1e-2f * warp_sum(lane < NX ? fa * fa : 0.0f)) {
+                        // carried to stage k - 1 as the row F A on x_k, when the
+                        // inputs act on it there at scale (a position behind its
+                        // velocity sees them only through dt: its multiplier form
+                        // would cancel in FP32, so it stays with the augmented
+                        // Lagrangian)
+                        if (lane < NX) pFw[nw * XP + lane] = fa;
+                        if (lane == 0) {
+                            pdw[nw] = d - fe;
+                            pow_[nw] = org;
+                        }
+                        ++nw;
+                    } else if (org / NX == k) {
+                        alm |= 1u << (org % NX);
+                    } else if (lane == 0) {
+                        atomicOr(c.albits() + org / NX, 1u << (org % NX));
+                    }
+                    __syncwarp();
                 }
-                if (tid >= nd && tid < kNCB) slot_i[tid] = -1;
-                // the others: augmented-Lagrangian terms in the stage cost
-                if (tid < NX && ((am >> tid) & 1u)) {
+                if (lane == 0) pn[1 - rd] = nw;
+                if (lane < NX && ((alm >> lane) & 1u)) {
                     float bnd;
                     bool up;
-                    c.box_active(k, tid, &bnd, &up);
-                    const float qq = s[D::oQ + tid], pen = c.rhob()[k * NX + tid];
+                    c.box_active(k, lane, &bnd, &up);
+                    const float qq = s[D::oQ + lane], pen = c.rhob()[k * NX + lane];
                     const float qn = qq + pen;
-                    s[D::oRY + tid] = (fmaf(qq, s[D::oRY + tid], pen * bnd) - c.nub()[k * NX + tid]) / qn;
-                    s[D::oQ + tid] = qn;
+                    s[D::oRY + lane] = (fmaf(qq, s[D::oRY + lane], pen * bnd) - c.nub()[k * NX + lane]) / qn;
+                    s[D::oQ + lane] = qn;
                 }
-                if (tid == 0) c.dbits()[k] = dm;
+                if (lane == 0) pn[2] = nd;
             }
             __syncthreads();
             for (int e = tid; e < NX * XP + NX; e += kPT) {
@@ -407,7 +497,7 @@ __device__ int cta_polish(const CCtx<D>& c) {
                     sv[r] = fmaf(s[D::oQ + r], s[D::oRY + r], Xp[r * XP + NX]);
                 }
             }
-            cmask = (1u << __popc(c.dbits()[k])) - 1u;
+            cmask = (1u << pn[2]) - 1u;
             __syncthreads();
         }
         const uint32_t fmask = freep[0];
@@ -473,27 +563,29 @@ __device__ int cta_polish(const CCtx<D>& c) {
             }
         }
         if constexpr (BOX) {
-            // the bound rows NU + t of [M | RHS]: [Bt_i | 0 | -A_i | b_i - et_i],
-            // and the bound columns NU + t: Bt_i' (a unit pivot for a free slot)
-            const int* slot_i = reinterpret_cast<const int*>(sm + CS::oslot);
-            const float* slot_b = sm + CS::oslot + kNCB;
+            // the bound rows NU + t of [M | RHS]: [F Bt | 0 | -F A | d - F et],
+            // and the bound columns NU + t: (F Bt)' (a unit pivot for a free slot)
+            const float* sc = sm + CS::osc;
+            const float* sfb = sm + CS::osfb;
+            const float* saff = sm + CS::osaff;
+            const int nd = reinterpret_cast<const int*>(sm + CS::opn)[2];
             constexpr int NR = NU + kNCB, WB = NR + NK;
             for (int e = tid; e < kNCB * WB; e += kPT) {
-                const int t = e / WB, col = e % WB, i = slot_i[t];
+                const int t = e / WB, col = e % WB;
                 float v = 0.0f;
-                if (i < 0) {
+                if (t >= nd) {
                     v = (col == NU + t) ? 1.0f : 0.0f;
                 } else if (col < NU) {
-                    v = BtT[col * XP + i];
+                    v = sc[t * 32 + col];
                 } else if (col >= NR) {
                     const int cc = col - NR;
-                    v = cc < NX ? -s[D::oA + i * NX + cc] : slot_b[t] - et[i];
+                    v = cc < NX ? sfb[t * XP + cc] : saff[t];
                 }
                 MC[col * CP + NU + t] = v;
             }
             for (int e = tid; e < kNCB * NU; e += kPT) {
-                const int t = e / NU, a = e % NU, i = slot_i[t];
-                MC[(NU + t) * CP + a] = i < 0 ? 0.0f : BtT[a * XP + i];
+                const int t = e / NU, a = e % NU;
+                MC[(NU + t) * CP + a] = t < nd ? sc[t * 32 + a] : 0.0f;
             }
         }
         __syncthreads();
@@ -629,8 +721,8 @@ __device__ int cta_polish(const CCtx<D>& c) {
             }
         }
         __syncthreads();
-        // (6) GR = [G | g2]: G = SA + SB K (+ E'K_lambda for exactly held bounds),
-        //     g2 = dv - SB kappa (- E'kappa_lambda); thread (row r, column quad
+        // (6) GR = [G | g2]: G = SA + SB K (+ F'K_lambda for exactly held rows),
+        //     g2 = dv - SB kappa (- F'kappa_lambda); thread (row r, column quad
         //     cq, half h of the inputs), halves combined by a shuffle
         {
             const int h = tid & 1, cq = (tid >> 1) & 3, r = tid >> 3;
@@ -661,18 +753,17 @@ __device__ int cta_polish(const CCtx<D>& c) {
                     o[q] = cc < NX ? SAT[cc * XP + r] + o[q] : (cc == NX ? dv[r] - o[q] : 0.0f);
                 }
                 if constexpr (BOX) {
-                    // a bound held exactly on component r: G_r += K_lambda, g2_r -= kappa_lambda
-                    const int* slot_i = reinterpret_cast<const int*>(sm + CS::oslot);
+                    // exactly held rows F: G += F'K_lambda, g2 -= F'kappa_lambda
+                    const float* sF = sm + CS::osF;
                     const float* Kl = sm + CS::oKl;
+                    const int nd = reinterpret_cast<const int*>(sm + CS::opn)[2];
+                    for (int t = 0; t < nd; ++t) {
+                        const float f = sF[t * XP + r];
 #pragma unroll
-                    for (int t = 0; t < kNCB; ++t) {
-                        if (slot_i[t] == r) {
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const int cc = 4 * cq + q;
-                                if (cc < NX) o[q] += Kl[t * XP + cc];
-                                else if (cc == NX) o[q] -= Kl[t * XP + NX];
-                            }
+                        for (int q = 0; q < 4; ++q) {
+                            const int cc = 4 * cq + q;
+                            if (cc < NX) o[q] = fmaf(f, Kl[t * XP + cc], o[q]);
+                            else if (cc == NX) o[q] = fmaf(-f, Kl[t * XP + NX], o[q]);
                         }
                     }
                 }
@@ -729,17 +820,14 @@ __device__ int cta_polish(const CCtx<D>& c) {
             for (int r = 0; r < NX; ++r) acc = fmaf(Ks[tid * NK + r], xk[r], acc);
             ut[tid] = acc;
         } else if (BOX && tid < NU + kNCB) {
-            // the multiplier of the exactly held bound in slot t (its component
-            // the t-th set bit of the stage's dbits), lambda = K_lambda x + kappa_lambda
-            const int t = tid - NU;
-            uint32_t dm = c.dbits()[k];
-            if (t < __popc(dm)) {
-                for (int q = 0; q < t; ++q) dm &= dm - 1u;
-                const int i = __ffs(dm) - 1;
+            // the multiplier of the exactly held row in slot t, lambda =
+            // K_lambda x + kappa_lambda, is the multiplier of its bound
+            const int t = tid - NU, org = c.sorig()[k * kNCB + t];
+            if (org >= 0) {
                 float acc = Ks[(NU + t) * NK + NX];
 #pragma unroll
                 for (int r = 0; r < NX; ++r) acc = fmaf(Ks[(NU + t) * NK + r], xk[r], acc);
-                c.nub()[k * NX + i] = acc;
+                c.nub()[org] = acc;
             }
         }
         __syncthreads();
@@ -822,7 +910,10 @@ __device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
     constexpr int NX = D::NX;
     bool any = false;
     if constexpr (BOX) {
-        for (int k = c.tid; k < c.Nh; k += kPT) any |= c.sbits()[k] != 0u;
+        for (int k = c.tid; k < c.Nh; k += kPT) {
+            any |= c.sbits()[k] != 0u;
+            c.albits()[k] = 0u;  // every bound first tries to be held exactly
+        }
         any = __syncthreads_or(any);
     }
     int npiv = 0;
@@ -835,19 +926,16 @@ __device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
             const int k = e / NX, i = e % NX;
             float bnd;
             bool up;
-            if (c.box_active(k, i, &bnd, &up)) {
+            if (c.box_active(k, i, &bnd, &up) && !((c.dbits()[k] >> i) & 1u)) {
+                // held by the augmented Lagrangian (an exactly held bound has
+                // its multiplier from the scan, and more scans cannot improve it)
                 const float d = c.xr()[(k + 1) * NX + i] - bnd;
                 const float vi = fabsf(d) / (1.0f + fabsf(bnd));
-                if (!((c.dbits()[k] >> i) & 1u)) {
-                    // held by the augmented Lagrangian (an exactly held bound
-                    // has its multiplier from the scan)
-                    const float pen = c.rhob()[e];
-                    c.nub()[e] = fmaf(pen, d, c.nub()[e]);
-                    // a stiff bound (its violation falls too slowly) gets a larger penalty
-                    if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e])
-                        c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
-                    c.dprev()[e] = fabsf(d);
-                }
+                const float pen = c.rhob()[e];
+                c.nub()[e] = fmaf(pen, d, c.nub()[e]);
+                // a stiff bound (its violation falls too slowly) gets a larger penalty
+                if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e]) c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
+                c.dprev()[e] = fabsf(d);
                 viol = fmaxf(viol, vi);
             }
         }
