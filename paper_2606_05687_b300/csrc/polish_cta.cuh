@@ -5,8 +5,10 @@
 //                the remaining free components is solved by a backward
 //                Riccati scan (full-size per-stage systems whose eliminated
 //                columns are unit vectors, Gauss-Jordan over the free pivots
-//                only, operands in registers and 64-byte shared rows), then
-//                a forward rollout;
+//                only, operands in registers and 80-byte shared rows; with
+//                state boxes, active bounds as equality rows where inputs
+//                reach them, else an augmented Lagrangian), then a forward
+//                rollout;
 //   certificate: costate scan, stationarity, per-contact nonnegative
 //                multipliers (cyclic coordinate descent) and the KKT
 //                residual this implementation stops on (the paper gives only an
@@ -253,12 +255,13 @@ __device__ __forceinline__ float dot_reg(const float* a, const float (&v)[4 * ((
 // M is kept at full size: an eliminated column makes row and column of M a
 // unit vector and its row of the right-hand side zero, so its elimination
 // step is skipped and its gains come out zero.
-// With state bounds (BOX), an active bound b_i on component i of xi_{k+1}
-// whose row Bt_i is nonzero is an equality row of the stage's system,
-//   [M  Bt_I'] [ut    ]   [-Bt'S A | Bt'(s - S et) - gt]
-//   [Bt_I  0 ] [lambda] = [ -A_I   | b_I - et_I       ]  [x; 1],
-// lambda = K_lambda x + kappa_lambda its multiplier (L = f + lambda'(x_I - b_I)),
-// and then G += E_I'K_lambda, g2 -= E_I'kappa_lambda (E_I selects rows I).
+// With state bounds (BOX), the rows F of active bounds on x_{k+1} that the
+// stage's free inputs reach (F = e_i for a bound of this stage, or a row
+// carried back from a later stage) are equality rows of the stage's system,
+//   [M    (F Bt)'] [ut    ]   [-Bt'S A | Bt'(s - S et) - gt]
+//   [F Bt   0    ] [lambda] = [ -F A   | d - F et          ]  [x; 1],
+// lambda = K_lambda x + kappa_lambda their multipliers (L = f + lambda'(F x_{k+1} - d)),
+// and then G += F'K_lambda, g2 -= F'kappa_lambda.
 template <class D, bool BOX = false>
 __device__ int cta_polish(const CCtx<D>& c) {
     constexpr int NX = D::NX, NU = D::NU, NK = NX + 1;
