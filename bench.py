@@ -64,9 +64,9 @@ KERNEL_HEADERS = {
 }
 MEASURED_TRAFFIC = {
     # the polish kernel's round-0 launch (all 4096 instances), one ncu capture
-    "polish:74c8adcd89d6c216": 292320256,
+    "polish:27ac621d4bdacbec": 292913408,
     # the round kernel's round-0 launch, one ncu capture
-    "round:53073bba3b4e79fa": 439632896,
+    "round:e63eaccba2275979": 439286016,
 }
 
 
@@ -364,6 +364,51 @@ def receding_leg(args, parts, MixedSolver, pinmpc, W, torch, steps=6, timed_from
             "what": "receding-horizon steps of the uneven batch: data moved one stage, xi_0 / u_prev from the last "
                     "solution, warm start moved one stage, solves replayed from CUDA graphs; "
                     f"{steps - timed_from} timed steps after {timed_from} capture steps"}
+
+
+SWEEP_N = (10, 20, 40, 64)
+SWEEP_B = (64, 1024, 4096, 16384)
+
+
+def sweep_leg(pinmpc, W, torch, dev, reps=5):
+    """Solve time over the number of environments B and the horizon N (the
+    shape of the paper's Fig. 3 scalability sweep, on walking instances):
+    inputs resident, one batch in flight on one handle, CUDA events around
+    set_stages + solve + the status copy on the handle's stream; the median
+    of `reps` solves per point after one untimed solve.  Per point: the
+    certified and stalled counts (MPC_STALLED: a polished point within 4x of
+    the tolerance whose faces held) and the most iterations any instance ran."""
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    bmax = max(SWEEP_B)
+    for N in SWEEP_N:
+        full = W.generate(W.rl_scale_walking(B=bmax, N=N, seed=SEED + 11 + N))
+        t_full = pinmpc.device_inputs(full, dev)
+        s = pinmpc.solver_for(full)
+        st = torch.empty(bmax, dtype=torch.int32, device=dev)
+        it = torch.empty(bmax, dtype=torch.int32, device=dev)
+        for B in SWEEP_B:
+            times = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.set_stages(B, N, **t_full, stream=stream)
+                s.solve(B, stream=stream)
+                s.get_traj(None, None, st, it, None, None, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            cert = int((st[:B] == pinmpc.CONVERGED).sum().item())
+            med = statistics.median(times)
+            rows.append({"N": N, "B": B, "ms_per_solve": med, "certified": cert,
+                         "stalled": int((st[:B] == pinmpc.STALLED).sum().item()),
+                         "iters_max": int(it[:B].max().item()), "certified_per_s": cert / (med * 1e-3)})
+        s.close()
+        del t_full, full
+        torch.cuda.empty_cache()
+    return {"rows": rows, "what": "walking instances (8 point contacts), inputs resident, one batch in flight on one "
+                                  f"handle, median of {reps} solves per point (set_stages + solve + status copy)"}
 
 
 def run_gpu(args):
@@ -749,6 +794,8 @@ def run_gpu(args):
                                      "u_rel_max": float(np.max(e_p))}
         pa.close()
 
+    sweep = sweep_leg(pinmpc, W, torch, dev) if args.sweep and not args.device_only else None
+
     precision = None
     if not args.device_only:
         # reduced-precision caches (mpc_config.precision): the Gram products of
@@ -852,6 +899,7 @@ def run_gpu(args):
         "fleet": fleet,
         "plain_admm": plain,
         "precision": precision,
+        "sweep": sweep,
         "gpu_launches": int(sum(n for _, n in ktimes.values())),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": MEASURED_TRAFFIC.get(f"{dom}:{h}"),
@@ -909,6 +957,8 @@ def main():
     ap.add_argument("--device-only", action="store_true",
                     help="profiling aid: only the device-resident steps (no CPU baseline, no e2e leg); "
                          "the line it prints is not a bench result")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the solve over B in (64, 1024, 4096, 16384) and N in (10, 20, 40, 64)")
     args = ap.parse_args()
     INFLIGHT = max(1, args.inflight)
     if args.impl == "reference":

@@ -61,12 +61,18 @@ typedef enum mpc_status {
 /* Per-instance result codes written by mpc_get_traj's status array. */
 enum {
     MPC_CONVERGED = 0,  /* KKT certificate <= kkt_tol */
-    MPC_MAX_ITER = 1,   /* iteration cap reached; outputs are the last iterate */
+    MPC_MAX_ITER = 1,   /* iteration cap reached; outputs are the last iterate, or the best
+                           polished point if one came within 4 kkt_tol and closer */
     MPC_NONFINITE = 2,  /* NaN/Inf in this instance's inputs */
     MPC_BAD_SET = 3,    /* empty contact set (n_max < 0 or mu < 0 on a stance contact) */
     MPC_TIMEOUT = 4,    /* reserved for bounded device-side waits */
     MPC_BAD_HORIZON = 5, /* horizon[b] outside [1, N] */
     MPC_BAD_DIM = 6,     /* nu[b] not a multiple of contact_dim in [0, nu] */
+    MPC_STALLED = 7,     /* stopped before the cap: a polished point's certificate came
+                            within 4 kkt_tol and the faces of the iterate then held for two
+                            checks; outputs are that point, kkt its certificate (the FP32
+                            floor of the certificate rises with the horizon, so past ~40
+                            stages a few instances on the right faces sit above kkt_tol) */
     MPC_RUNNING = -1     /* not finished yet: read before the solve has passed
                             the round that finishes the instance */
 };

@@ -725,6 +725,11 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
     // every instance reads MPC_RUNNING (-1) until the round that finishes it
     if ((e = cudaMemsetAsync(h->out_status, 0xff, (size_t)B * sizeof(int), st)) != cudaSuccess)
         return cuda_fail(h, e, "cudaMemsetAsync");
+    // the polish keeps its best near-miss point's certificate in kkt (a huge
+    // value until there is one: bytes 0x7f are 3.4e38) and a stall count in iters
+    if ((e = cudaMemsetAsync(h->out_kkt, 0x7f, (size_t)B * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->out_iters, 0, (size_t)B * sizeof(int), st)) != cudaSuccess)
+        return cuda_fail(h, e, "cudaMemsetAsync");
     // per-stage factors and input checks for the whole batch
     {
         FactorArgs fa{};

@@ -81,6 +81,14 @@ constexpr float kBoxGrow = 10.0f;
 constexpr float kBoxRate = 0.1f;
 constexpr float kBoxPenaltyMax = 1e7f;
 constexpr int kBoxIters = 12;
+// A polished point whose certificate misses the tolerance by at most a
+// factor kStallBand is kept in the outputs; when kStallChecks later checks
+// bring no improvement (the faces of the ADMM iterate unchanged, or a polish
+// that does not halve the best certificate) the instance stops with that
+// point (the FP32 floor of the certificate rises with the horizon: past ~40
+// stages a few instances on the right faces sit above it)
+constexpr float kStallBand = 4.0f;
+constexpr int kStallChecks = 2;
 constexpr float kBoxViol = 1e-7f;
 // At most this many active state bounds per stage are held exactly in the
 // polish (an equality row added to the KKT system of a stage whose free

@@ -1147,12 +1147,12 @@ __device__ bool cta_refine_modes(const CCtx<D>& c, float alpha) {
     return __syncthreads_or(changed);
 }
 
+// The point (xi, u, active faces, certificate) of instance b into the
+// outputs; zeros and an infinite certificate when !ok.
 template <class D>
-__device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, int status, int iters, float kkt,
-                                 int npol) {
+__device__ void cta_write_point(const CCtx<D>& c, const RoundArgs& a, int b, bool ok, float kkt) {
     constexpr int NX = D::NX, NU = D::NU, CD = D::CD, M = D::M, F = D::F;
     const int Nv = a.N;
-    const bool ok = status == kConverged || status == kMaxIter;
     float* oxi = a.out_xi + (size_t)b * Nv * NX;
     float* ou = a.out_u + (size_t)b * Nv * NU;
     for (int e = c.tid; e < Nv * NX; e += kPT) {
@@ -1188,13 +1188,24 @@ __device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, in
         }
         a.out_bits[(size_t)b * Nv + k] = bits;
     }
-    if (c.tid == 0) {
+    if (c.tid == 0) a.out_kkt[b] = ok ? kkt : INFINITY;
+}
+
+// Final status of instance b (its point already in the outputs).
+__device__ __forceinline__ void finish_instance(const RoundArgs& a, int b, int status, int iters, int npol) {
+    if (threadIdx.x == 0) {
         a.out_status[b] = status;
         a.out_iters[b] = iters;
-        a.out_kkt[b] = ok ? kkt : INFINITY;
         a.out_npol[b] = npol;
         a.done[b] = 1;
     }
+}
+
+template <class D>
+__device__ void cta_write_output(const CCtx<D>& c, const RoundArgs& a, int b, int status, int iters, float kkt,
+                                 int npol) {
+    cta_write_point<D>(c, a, b, status == kConverged || status == kMaxIter, kkt);
+    finish_instance(a, b, status, iters, npol);
 }
 
 // Polish / certify / refine after a round: one CTA per instance.
@@ -1245,6 +1256,17 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
     int npol = a.out_npol[b];
     int npiv = a.out_piv[b];
     float kkt = INFINITY;
+    // the outputs hold the best polished point within kStallBand of the
+    // tolerance so far (its certificate in kkt; the solve starts with a huge
+    // value) and, in iters, a stall count (the solve starts with 0): checks
+    // since there is such a point at which the faces did not change or the
+    // polish did not halve the best certificate; thread 0 reads and writes
+    // both and shares its decisions through a barrier
+    if (a.polish && !changed &&
+        __syncthreads_or(c.tid == 0 && a.out_kkt[b] <= kStallBand * a.kkt_tol && a.out_iters[b] + 1 >= kStallChecks)) {
+        finish_instance(a, b, kStalled, a.m1, npol);
+        return;
+    }
     if (a.polish && changed) {
         for (int e = c.tid; e < c.Nh * D::NC; e += kPT) glast[e] = c.modes[e];
         if constexpr (BOX) {
@@ -1261,6 +1283,30 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         if (c.tid == 0) a.out_piv[b] = npiv;
         if (kkt <= a.kkt_tol) {
             cta_write_output<D>(c, a, b, kConverged, a.m1, kkt, npol);
+            return;
+        }
+        // thread 0: keep the point if it is the closest miss within the band
+        // so far; a point that halves the best restarts the stall count,
+        // another one within the band advances it like a check without a
+        // polish.  With state bounds every polish within the band restarts
+        // it and one outside the band holds it off (their augmented
+        // Lagrangian restarts from the iterate's multipliers, so later
+        // polishes on the same faces still move)
+        float* flag = c.sm + CtaSmem<D>::ored;
+        if (c.tid == 0) {
+            const float best = a.out_kkt[b];
+            const bool inb = kkt <= kStallBand * a.kkt_tol;
+            const int stall = BOX ? (inb ? 0 : -(1 << 20))
+                                  : ((inb && kkt < 0.5f * best) ? 0 : a.out_iters[b] + (inb ? 1 : 0));
+            a.out_iters[b] = stall;
+            flag[0] = (inb && kkt < best) ? 1.0f : 0.0f;
+            flag[1] = stall >= kStallChecks ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+        const bool stop = flag[1] != 0.0f;
+        if (flag[0] != 0.0f) cta_write_point<D>(c, a, b, true, kkt);
+        if (stop) {
+            finish_instance(a, b, kStalled, a.m1, npol);
             return;
         }
     }
@@ -1281,12 +1327,21 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         }
         cta_rollout<D>(c);
         kkt = cta_certificate<D, BOX>(c);
-        if (kkt <= a.kkt_tol || final_round) {
-            cta_write_output<D>(c, a, b, kkt <= a.kkt_tol ? kConverged : kMaxIter, a.m1, kkt, npol);
+        if (kkt <= a.kkt_tol) {
+            cta_write_output<D>(c, a, b, kConverged, a.m1, kkt, npol);
+            return;
+        }
+        if (final_round) {
+            // the iterate, unless a polished point came closer
+            if (__syncthreads_or(c.tid == 0 && kkt <= a.out_kkt[b])) cta_write_point<D>(c, a, b, true, kkt);
+            finish_instance(a, b, kMaxIter, a.m1, npol);
             return;
         }
     }
     if (c.tid == 0) {
+        // a check without a polish advances the stall count once there is a
+        // point within the band
+        if (a.polish && !changed && a.out_kkt[b] <= kStallBand * a.kkt_tol) a.out_iters[b] += 1;
         a.out_npol[b] = npol;
         // still running: next round, in its horizon class's list
         const int cl = horizon_class(c.Nh, a.N, a.ncls, a.cls_cap);

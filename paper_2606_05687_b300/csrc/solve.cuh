@@ -29,7 +29,8 @@
 
 namespace pinmpc {
 
-enum : int { kConverged = 0, kMaxIter = 1, kNonFinite = 2, kBadSet = 3, kTimeout = 4, kBadHorizon = 5, kBadDim = 6 };
+enum : int { kConverged = 0, kMaxIter = 1, kNonFinite = 2, kBadSet = 3, kTimeout = 4, kBadHorizon = 5, kBadDim = 6,
+             kStalled = 7 };
 
 // mode word of one contact after the projection (bit layout):
 //   bit 2j   : tangential j clamped at +c_j n     bit 2j+1 : clamped at -c_j n

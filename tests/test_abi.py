@@ -56,6 +56,19 @@ def test_struct_layout_matches_header(tmp_path, P):
     assert got == want
 
 
+def test_status_codes_match_header(tmp_path, P):
+    names = ["MPC_CONVERGED", "MPC_MAX_ITER", "MPC_NONFINITE", "MPC_BAD_SET", "MPC_TIMEOUT", "MPC_BAD_HORIZON",
+             "MPC_BAD_DIM", "MPC_STALLED", "MPC_RUNNING"]
+    src = tmp_path / "codes.c"
+    src.write_text("\n".join(['#include <stdio.h>', '#include "pinmpc.h"', "int main(void){"] +
+                             [f'printf("%d\\n", (int){n});' for n in names] + ["return 0;}"]))
+    exe = tmp_path / "codes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert got == [P.CONVERGED, P.MAX_ITER, P.NONFINITE, P.BAD_SET, P.TIMEOUT, P.BAD_HORIZON, P.BAD_DIM,
+                   P.STALLED, P.RUNNING]
+
+
 def test_defaults_and_limits(P):
     cfg = P.default_config(13, 8, 3, 4096, 20)
     assert cfg.rho == 100.0 and cfg.u_scale == 300.0 and cfg.kkt_tol == pytest.approx(2e-6)

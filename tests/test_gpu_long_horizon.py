@@ -2,8 +2,9 @@
 of two CTAs per instance, half of the stages in each.  Parity with the
 oracle for ragged horizons U{5..40}, for the edge horizons 1, 2, 3, 33, 63
 and 64 of a 64-stage batch (one CTA of the pair empty; the 640- and the
-1024-thread forms), a warm restart at 40 stages, and instances of 32 stages
-or fewer, which a 32-stage handle solves with the one-CTA form."""
+1024-thread forms), a warm restart at 40 stages, instances of 32 stages
+or fewer, which a 32-stage handle solves with the one-CTA form, and the
+stall stop of an instance whose certificate sits at its FP32 floor."""
 import dataclasses
 
 import numpy as np
@@ -11,7 +12,9 @@ import pytest
 
 from paper_2606_05687_b300 import workload as W
 
-from parity_util import REL_TRAJ, compare, oracle_refs
+from oracle import kkt as okkt
+from oracle import qp
+from parity_util import KKT_TOL, OBJ_GAP, REL_TRAJ, compare, oracle_refs
 
 pytestmark = pytest.mark.gpu
 
@@ -85,3 +88,38 @@ def test_warm_restart_40(pinmpc):
     refs = oracle_refs(batch, ids)
     compare(batch, cold, ids, refs)
     compare(batch, warm, ids, refs)
+
+
+def test_stalled_instance_returns_its_polished_point(pinmpc):
+    """Past ~40 stages the FP32 floor of the certificate can sit just above
+    kkt_tol on the right faces: instance 54 of this 48-stage walking batch
+    polishes to a point 1e-6 from the optimum whose certificate is 2.5e-6
+    against the 2e-6 tolerance, and no later polish can do better (the
+    faces of the iterate do not change).  It stops once its faces have held
+    for two checks after that polish, with status STALLED and the polished
+    point, which meets the oracle bars; it used to run to the iteration cap
+    and return the ADMM iterate (KKT 0.57).  No instance of the batch ends
+    at the cap."""
+    batch = W.generate(W.rl_scale_walking(B=1024, N=48, seed=125))
+    out = pinmpc.solve_workload(batch)
+    st = out["status"]
+    assert set(np.unique(st).tolist()) <= {pinmpc.CONVERGED, pinmpc.STALLED}, np.unique(st)
+    sub = batch.subset([54])
+    s = pinmpc.solver_for(sub)
+    tol, cap = s.cfg.kkt_tol, s.cfg.max_iter
+    one = pinmpc.solve_workload(sub, solver=s)
+    s.close()
+    assert st[54] == pinmpc.STALLED and one["status"][0] == pinmpc.STALLED
+    assert one["iters"][0] < cap
+    assert tol < one["kkt"][0] <= 4 * tol
+    inst = qp.instance(sub, 0)
+    sol = qp.solve_instance(inst)
+    u = one["u"][0].astype(np.float64)
+    xi = one["xi"][0].astype(np.float64)
+    rep = okkt.kkt_residual(inst, xi, u)
+    assert np.abs(u - sol.u).max() <= REL_TRAJ * np.abs(sol.u).max()
+    assert np.abs(xi - sol.xi).max() <= REL_TRAJ * np.abs(sol.xi).max()
+    assert rep.kkt <= KKT_TOL
+    assert abs(qp.objective(inst, xi, u) - sol.objective) <= OBJ_GAP * abs(sol.objective)
+    # the device certificate is the oracle checker's figure
+    assert abs(one["kkt"][0] - rep.kkt) <= 0.2 * rep.kkt + 5e-7

@@ -8,7 +8,8 @@ of mantissa in the caches, so its ADMM reads faces off a coarser fixed
 point; the polish still certifies what it returns, but an instance may run
 out of iterations (measured: 1 of 64 foot-wrench instances at max_iter
 1000).  BF16 may therefore leave up to 2 % uncertified, reported as
-MPC_MAX_ITER, never as a converged wrong answer; every certified instance
+MPC_MAX_ITER or MPC_STALLED with the certificate above the tolerance, never
+as a converged wrong answer; every certified instance
 must match the oracle.  The per-instance error against the oracle is
 reported beside the FP32 one.  The rounded caches
 do change the ADMM iteration: one iteration from a loaded iterate departs
@@ -38,7 +39,9 @@ def test_every_precision_certifies_and_matches_the_oracle(mode, maker, B, N):
     out = pinmpc.solve_workload(batch, precision=MODES[mode])
     ok = out["status"] == pinmpc.CONVERGED
     if mode == "bf16":
-        assert (~ok).sum() <= max(1, B // 50) and np.all(out["status"][~ok] == pinmpc.MAX_ITER)
+        assert (~ok).sum() <= max(1, B // 50)
+        assert np.all(np.isin(out["status"][~ok], [pinmpc.MAX_ITER, pinmpc.STALLED]))
+        assert np.all(out["kkt"][~ok] > 2e-6)
     else:
         assert np.all(ok), np.flatnonzero(~ok)
     assert out["kkt"][ok].max() <= 1e-5

@@ -21,10 +21,11 @@ velocity (the CoM height) is held by an augmented Lagrangian whose multiplier co
 h / (h + penalty), h the cost of moving the component (up to 3e6 for the CoM
 height); its penalty grows until the bound holds, capped at 1e7 where FP32
 Riccati sums lose the other terms, so CoM-height boxes mostly stop at the
-iteration cap and say so (MPC_MAX_ITER, certificate above the tolerance).
+iteration cap, or stall on their faces, and say so (MPC_MAX_ITER or
+MPC_STALLED, certificate above the tolerance).
 Measured over 20 seeds of these batches (B300): vertical-velocity boxes
 320/320 (walking) and 220/220 (foot wrenches) certified, forward-velocity
-boxes 320/320 and 200/200, CoM-height boxes 31/320 and 5/220.  Every
+boxes 320/320 and 200/200, CoM-height boxes 30/320 and 5/220.  Every
 certified instance must match the oracle."""
 import numpy as np
 import pytest
@@ -109,8 +110,9 @@ def test_state_boxes_match_the_oracle(maker, B, N):
     st = out["status"]
     s.close()
     ok = st == pinmpc.CONVERGED
-    # honest statuses: an uncertified instance reports the cap with its certificate above the tolerance
-    assert np.all(ok | (st == pinmpc.MAX_ITER)) and np.all(out["kkt"][~ok] > 2e-6)
+    # honest statuses: an uncertified instance reports the cap or a stall
+    # with its certificate above the tolerance
+    assert np.all(ok | (st == pinmpc.MAX_ITER) | (st == pinmpc.STALLED)) and np.all(out["kkt"][~ok] > 2e-6)
     by_type = [int(ok[t::3].sum()) for t in range(3)]
     n_type = [len(ok[t::3]) for t in range(3)]
     assert by_type[0] >= 0.9 * n_type[0], by_type  # vertical velocity, held exactly: 100 % over 20 seeds
@@ -169,8 +171,8 @@ def test_many_bounds_per_stage_stay_finite():
     """Bounds on all six velocity components at every stage: more than the
     kNCB rows a stage holds exactly, and rows that are dependent where few
     inputs are free (the rank check hands those to the augmented
-    Lagrangian).  Every output is finite, every status honest (CONVERGED or
-    MAX_ITER), and the instances that certify match the oracle."""
+    Lagrangian).  Every output is finite, every status honest (CONVERGED,
+    MAX_ITER or STALLED), and the instances that certify match the oracle."""
     TA.ensure_lib()
     batch = W.generate(W.rl_scale_walking(B=24, N=10, seed=1404, e_scale=0.02))
     free = pinmpc.solve_workload(batch)
@@ -188,7 +190,7 @@ def test_many_bounds_per_stage_stay_finite():
     st = out["status"]
     for k in ("xi", "u", "kkt"):
         assert np.all(np.isfinite(out[k])), k
-    assert np.all((st == pinmpc.CONVERGED) | (st == pinmpc.MAX_ITER))
+    assert np.all((st == pinmpc.CONVERGED) | (st == pinmpc.MAX_ITER) | (st == pinmpc.STALLED))
     # tight boxes on all six velocities at once: most instances stop at the
     # iteration cap (the point of the test is that nothing turns non-finite)
     ok = [b for b in range(B) if st[b] == pinmpc.CONVERGED]

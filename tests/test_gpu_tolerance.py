@@ -6,7 +6,8 @@ oracle checker evaluated in the same normalisation, and every certified
 solution still matches the oracle.  An absolute part far below the
 relative one (1e-3 of it) asks for residuals near FP32 rounding on the
 small-scale terms; instances that cannot reach it stop at the iteration cap
-and say so (MPC_MAX_ITER with their certificate above the tolerance)."""
+or stall on their faces and say so (MPC_MAX_ITER or MPC_STALLED with their
+certificate above the tolerance)."""
 import numpy as np
 import pytest
 
@@ -28,11 +29,11 @@ def test_absolute_part_of_the_tolerance(ratio):
     tol = 2e-6
     out = pinmpc.solve_workload(batch, kkt_tol=tol, kkt_tol_abs=ratio * tol)
     st = out["status"]
-    assert np.all((st == pinmpc.CONVERGED) | (st == pinmpc.MAX_ITER))
+    assert np.all((st == pinmpc.CONVERGED) | (st == pinmpc.MAX_ITER) | (st == pinmpc.STALLED))
     if ratio >= 1.0:
         assert np.all(st == pinmpc.CONVERGED), np.flatnonzero(st)
     # an uncertified instance says so: its certificate is above the tolerance
-    assert np.all(out["kkt"][st == pinmpc.MAX_ITER] > tol)
+    assert np.all(out["kkt"][st != pinmpc.CONVERGED] > tol)
     ids = [b for b in range(0, 128, 8) if st[b] == pinmpc.CONVERGED]
     for b in ids:
         inst = qp.instance(batch, b)
