@@ -180,6 +180,10 @@ bool pick_shape(int nx, int nc, int cd, Shape* out) {
 }
 
 constexpr int kSmemLimit = 227 * 1024;
+// factor on the refinement step from the fifth round on (rounds 0-3 keep the
+// configured step): the instances still running there are mostly caught in
+// an active-set cycle of the refinement, which the longer step breaks
+constexpr float kRefineAlphaLate = 3.0f;
 
 int max_optin_smem(int device) {
     int v = 0;
@@ -783,6 +787,9 @@ static mpc_status enqueue_solve(mpc_handle* h, int32_t B, RoundArgs r, cudaStrea
         // the few instances left after two rounds get more refinement: the
         // allowance doubles per round from round 2 on (up to 32)
         r.refine_steps = std::min(32, c.refine_steps << std::min(std::max(round - 1, 0), 4));
+        // and from round 4 on a longer step, which breaks the refinement's
+        // active-set cycles (faces flipped in and out again)
+        r.refine_alpha = round >= 4 ? kRefineAlphaLate * c.refine_alpha : c.refine_alpha;
         if ((e = cudaMemsetAsync(cursor, 0, K * sizeof(int), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(r.cnt_out, 0, K * sizeof(int), st)) != cudaSuccess)
             return cuda_fail(h, e, "cudaMemsetAsync");
