@@ -63,7 +63,7 @@ struct CtaSmem {
                          oScanEnd = al(opn + 4),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + (NU + kNCB) * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
-                         ored = al(obuf1 + D::SREC), oFixed = al(ored + 32);
+                         ored = al(obuf1 + D::SREC), ostep = al(ored + 32), oFixed = al(ostep + 4);  // ostep: the refinement step's state
     static_assert(NU + NK <= 48, "pivot-row buffer");
     // column stride of the column-major [M | RHS]: a multiple of 4 at least NU
     // with an odd number of float4s, so consecutive columns read as float4
@@ -1275,10 +1275,30 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         }
         npiv += cta_polish_box<D, BOX>(c, &npol);
         kkt = cta_certificate<D, BOX>(c);
+        // the refinement step, the best certificate of this call and the
+        // refinements since it improved: from the second refinement in a row
+        // that does not improve on it each next step is 3x longer (up to 27x),
+        // which breaks active-set cycles (faces flipped in and out again); an
+        // improvement restores the configured step.  Kept in shared memory,
+        // written by thread 0
+        float* step = c.sm + CtaSmem<D>::ostep;
+        if (c.tid == 0) {
+            step[0] = a.refine_alpha;
+            step[1] = kkt;
+            step[2] = 0.0f;
+        }
         for (int r = 0; kkt > a.kkt_tol && r < a.refine_steps; ++r) {
-            if (!cta_refine_modes<D, BOX>(c, a.refine_alpha)) break;
+            __syncthreads();
+            if (!cta_refine_modes<D, BOX>(c, step[0])) break;
             npiv += cta_polish_box<D, BOX>(c, &npol);
             kkt = cta_certificate<D, BOX>(c);
+            if (c.tid == 0) {
+                const bool better = kkt < step[1];
+                step[2] = better ? 0.0f : step[2] + 1.0f;
+                step[0] = better ? a.refine_alpha
+                                 : (step[2] >= 2.0f ? fminf(3.0f * step[0], 27.0f * a.refine_alpha) : step[0]);
+                step[1] = fminf(step[1], kkt);
+            }
         }
         if (c.tid == 0) a.out_piv[b] = npiv;
         if (kkt <= a.kkt_tol) {
