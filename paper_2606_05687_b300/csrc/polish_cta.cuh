@@ -63,7 +63,7 @@ struct CtaSmem {
                          oScanEnd = al(opn + 4),
                          // forward rollout and certificate
                          oK = oScanEnd, out = al(oK + (NU + kNCB) * NK), obuf0 = al(out + NU), obuf1 = al(obuf0 + D::SREC),
-                         ored = al(obuf1 + D::SREC), ostep = al(ored + 32), oFixed = al(ostep + 4);  // ostep: the refinement step's state
+                         ored = al(obuf1 + D::SREC), ostep = al(ored + 32), oFixed = al(ostep + 16);  // ostep: the refinement's state
     static_assert(NU + NK <= 48, "pivot-row buffer");
     // column stride of the column-major [M | RHS]: a multiple of 4 at least NU
     // with an odd number of float4s, so consecutive columns read as float4
@@ -1147,6 +1147,33 @@ __device__ bool cta_refine_modes(const CCtx<D>& c, float alpha) {
     return __syncthreads_or(changed);
 }
 
+// A 32-bit hash of the faces being polished (and, with state bounds, of the
+// active bounds): each entry mixed with its index by the murmur3 finaliser,
+// the results XORed over the CTA (valid in every thread).
+template <class D, bool BOX>
+__device__ uint32_t cta_faces_hash(const CCtx<D>& c) {
+    auto mix = [](uint32_t x) {
+        x ^= x >> 16;
+        x *= 0x85EBCA6Bu;
+        x ^= x >> 13;
+        x *= 0xC2B2AE35u;
+        return x ^ (x >> 16);
+    };
+    uint32_t h = 0u;
+    for (int e = c.tid; e < c.Nh * D::NC; e += kPT) h ^= mix(c.modes[e] ^ ((uint32_t)(e + 1) * 0x9E3779B9u));
+    if constexpr (BOX)
+        for (int k = c.tid; k < c.Nh; k += kPT) h ^= mix(c.sbits()[k] ^ ((uint32_t)(k + 1) * 0x7F4A7C15u));
+    h = __reduce_xor_sync(0xffffffffu, h);
+    uint32_t* red = reinterpret_cast<uint32_t*>(c.sm + CtaSmem<D>::ored);
+    __syncthreads();
+    if (c.lane == 0) red[c.warp] = h;
+    __syncthreads();
+    uint32_t r = 0u;
+#pragma unroll
+    for (int w = 0; w < kPT / 32; ++w) r ^= red[w];
+    return r;
+}
+
 // The point (xi, u, active faces, certificate) of instance b into the
 // outputs; zeros and an infinite certificate when !ok.
 template <class D>
@@ -1281,15 +1308,43 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         // which breaks active-set cycles (faces flipped in and out again); an
         // improvement restores the configured step.  Kept in shared memory,
         // written by thread 0
+        // The hashes of the face sets polished in this call (a ring of 8 and
+        // its count): a refinement that lands on one of them is retried with
+        // a 3x longer step (twice at most) instead of polishing it again.
         float* step = c.sm + CtaSmem<D>::ostep;
-        if (c.tid == 0) {
-            step[0] = a.refine_alpha;
-            step[1] = kkt;
-            step[2] = 0.0f;
+        uint32_t* ring = reinterpret_cast<uint32_t*>(step + 4);
+        {
+            const uint32_t h0 = cta_faces_hash<D, BOX>(c);
+            if (c.tid == 0) {
+                step[0] = a.refine_alpha;
+                step[1] = kkt;
+                step[2] = 0.0f;
+                ring[0] = h0;
+                ring[8] = 1u;
+            }
         }
         for (int r = 0; kkt > a.kkt_tol && r < a.refine_steps; ++r) {
             __syncthreads();
-            if (!cta_refine_modes<D, BOX>(c, step[0])) break;
+            bool fresh = false;
+            float alpha = step[0];
+            for (int t = 0; t < 3; ++t) {
+                if (!cta_refine_modes<D, BOX>(c, alpha)) break;
+                const uint32_t h = cta_faces_hash<D, BOX>(c);
+                const uint32_t n = min(ring[8], 8u);
+                bool seen = false;
+                for (uint32_t i = 0; i < n; ++i) seen |= ring[i] == h;
+                if (!seen) {
+                    fresh = true;
+                    __syncthreads();
+                    if (c.tid == 0) {
+                        ring[ring[8] & 7u] = h;
+                        ring[8] += 1u;
+                    }
+                    break;
+                }
+                alpha *= 3.0f;
+            }
+            if (!fresh) break;
             npiv += cta_polish_box<D, BOX>(c, &npol);
             kkt = cta_certificate<D, BOX>(c);
             if (c.tid == 0) {
