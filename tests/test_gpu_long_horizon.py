@@ -3,8 +3,9 @@ of two CTAs per instance, half of the stages in each.  Parity with the
 oracle for ragged horizons U{5..40}, for the edge horizons 1, 2, 3, 33, 63
 and 64 of a 64-stage batch (one CTA of the pair empty; the 640- and the
 1024-thread forms), a warm restart at 40 stages, instances of 32 stages
-or fewer, which a 32-stage handle solves with the one-CTA form, and the
-stall stop of an instance whose certificate sits at its FP32 floor."""
+or fewer, which a 32-stage handle solves with the one-CTA form, the
+stall stop of an instance whose certificate sits at its FP32 floor, and an
+instance whose refinement used to cycle through face sets."""
 import dataclasses
 
 import numpy as np
@@ -123,3 +124,19 @@ def test_stalled_instance_returns_its_polished_point(pinmpc):
     assert abs(qp.objective(inst, xi, u) - sol.objective) <= OBJ_GAP * abs(sol.objective)
     # the device certificate is the oracle checker's figure
     assert abs(one["kkt"][0] - rep.kkt) <= 0.2 * rep.kkt + 5e-7
+
+
+def test_refinement_breaks_an_active_set_cycle(pinmpc):
+    """Instance 2859 of this 64-stage walking batch cycled through face sets
+    in the refinement (89 polishes) and certified only at the last check,
+    iteration 1000.  A longer refinement step after two refinements in a row
+    that do not improve the certificate, a face set already polished in the
+    call retried with a longer step, and the longer step from round 4 on
+    certify it at iteration 152 (12 polishes); the result matches the
+    oracle."""
+    batch = W.generate(W.rl_scale_walking(B=4096, N=64, seed=1077))
+    sub = batch.subset([2859])
+    out = pinmpc.solve_workload(sub)
+    assert out["status"][0] == pinmpc.CONVERGED
+    assert out["iters"][0] <= 312 and out["polishes"][0] <= 32, (out["iters"][0], out["polishes"][0])
+    compare(sub, out, [0])
