@@ -1302,15 +1302,15 @@ __device__ __forceinline__ void polish_instance(const RoundArgs& a, int b, float
         }
         npiv += cta_polish_box<D, BOX>(c, &npol);
         kkt = cta_certificate<D, BOX>(c);
-        // the refinement step, the best certificate of this call and the
-        // refinements since it improved: from the second refinement in a row
-        // that does not improve on it each next step is 3x longer (up to 27x),
-        // which breaks active-set cycles (faces flipped in and out again); an
-        // improvement restores the configured step.  Kept in shared memory,
-        // written by thread 0
-        // The hashes of the face sets polished in this call (a ring of 8 and
-        // its count): a refinement that lands on one of them is retried with
-        // a 3x longer step (twice at most) instead of polishing it again.
+        // The refinement's state, in shared memory and written by thread 0:
+        // the step, the best certificate of this call, the refinements since
+        // it improved, and the hashes of the face sets polished in this call
+        // (a ring of 8 and its count).  Against active-set cycles (faces
+        // flipped in and out again): from the second refinement in a row that
+        // does not improve the best certificate each next step is 3x longer
+        // (up to 27x), an improvement restores the configured step, and a
+        // refinement that lands on a face set already polished is retried
+        // with a 3x longer step (twice at most) instead of polishing it again.
         float* step = c.sm + CtaSmem<D>::ostep;
         uint32_t* ring = reinterpret_cast<uint32_t*>(step + 4);
         {
