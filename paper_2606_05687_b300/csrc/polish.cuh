@@ -90,6 +90,17 @@ constexpr int kBoxIters = 12;
 constexpr float kStallBand = 4.0f;
 constexpr int kStallChecks = 2;
 constexpr float kBoxViol = 1e-7f;
+// largest contraction rate from which the multiplier step extrapolates
+constexpr float kBoxAitkenMax = 0.95f;
+// weight of the certificate's terms of a state bound that the scan does not
+// hold exactly (its violation and |nu (x - b)|): a bound the inputs reach only
+// through a velocity (the CoM
+// height) is stiff, with a large multiplier, so a small violation moves u
+// (a relative 1.7e-6 was measured to move it by 3e-4) and a small slack on
+// the feasible side moves the objective (by nu times the slack: relative
+// gaps to 2.9e-6 at certificates near 1e-6); weighted 10x, a certified point
+// holds its bounds, and their complementarity, to a tenth of the tolerance
+constexpr float kBoxFeasWeight = 10.0f;
 // At most this many active state bounds per stage are held exactly in the
 // polish (an equality row added to the KKT system of a stage whose free
 // inputs move the bounded quantity); the others go through the augmented

@@ -72,7 +72,7 @@ struct CtaSmem {
     static constexpr int NRB = NU + kNCB;
     static constexpr int CP = (((NRB + 3) / 4) % 2 == 1) ? 4 * ((NRB + 3) / 4) : 4 * ((NRB + 3) / 4) + 4;
     static_assert(CP <= 32, "column buffer");
-    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, sbits, dbits, albits, sorig, total;
+    int xr, ur, y, wv, modes, cmu, cfm, cmask, nub, rhob, dprev, dlast, sbits, dbits, albits, sorig, total;
     __host__ __device__ explicit CtaSmem(int N) {
         int o = oFixed;
         auto take = [&o](int n) { int r = o; o += (n + 3) & ~3; return r; };
@@ -89,6 +89,7 @@ struct CtaSmem {
         nub = take(N * NX);   // signed multipliers of the active state bounds
         rhob = take(N * NX);  // their augmented-Lagrangian penalties
         dprev = take(N * NX); // their violations after the previous scan
+        dlast = take(N * NX); // and signed, when the penalty stayed (0: not comparable)
         sbits = take(N);      // active state bounds per stage (bit i lower, 16 + i upper)
         dbits = take(N);      // of those, the components held exactly by the last scan (bit i)
         albits = take(N);     // and those left to the augmented Lagrangian by this polish
@@ -145,6 +146,7 @@ struct CCtx {
     __device__ float* nub() const { return sm + L.nub; }
     __device__ float* rhob() const { return sm + L.rhob; }
     __device__ float* dprev() const { return sm + L.dprev; }
+    __device__ float* dlast() const { return sm + L.dlast; }
     __device__ uint32_t* sbits() const { return reinterpret_cast<uint32_t*>(sm + L.sbits); }
     __device__ uint32_t* dbits() const { return reinterpret_cast<uint32_t*>(sm + L.dbits); }
     __device__ uint32_t* albits() const { return reinterpret_cast<uint32_t*>(sm + L.albits); }
@@ -898,7 +900,11 @@ __device__ void cta_box_init(const CCtx<D>& c, const RoundArgs& a, int b) {
         c.nub()[e] = v;
         c.rhob()[e] = kBoxPenalty;
         c.dprev()[e] = INFINITY;
+        c.dlast()[e] = 0.0f;
     }
+    // no bound held exactly until a scan holds it (a certificate of the
+    // iterate weights every active bound as held by the augmented Lagrangian)
+    for (int k = c.tid; k < c.Nh; k += kPT) c.dbits()[k] = 0u;
     __syncthreads();
 }
 
@@ -935,9 +941,18 @@ __device__ int cta_polish_box(const CCtx<D>& c, int* nscan) {
                 const float d = c.xr()[(k + 1) * NX + i] - bnd;
                 const float vi = fabsf(d) / (1.0f + fabsf(bnd));
                 const float pen = c.rhob()[e];
-                c.nub()[e] = fmaf(pen, d, c.nub()[e]);
+                // while the penalty stays, the multiplier's error contracts by
+                // r = h / (h + p) per scan, and r = d / d_last: the step that
+                // lands on the limit is p d / (1 - r) (Aitken's extrapolation
+                // of the geometric sequence); a jump is not followed by another
+                const float dl = c.dlast()[e];
+                const float r = dl != 0.0f ? d / dl : 0.0f;
+                const bool jump = r > 0.0f && r < kBoxAitkenMax;
+                c.nub()[e] = fmaf(jump ? pen / (1.0f - r) : pen, d, c.nub()[e]);
                 // a stiff bound (its violation falls too slowly) gets a larger penalty
-                if (vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e]) c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
+                const bool grow = vi > kBoxViol && fabsf(d) > kBoxRate * c.dprev()[e] && pen < kBoxPenaltyMax;
+                if (grow) c.rhob()[e] = fminf(pen * kBoxGrow, kBoxPenaltyMax);
+                c.dlast()[e] = (grow || jump) ? 0.0f : d;
                 c.dprev()[e] = fabsf(d);
                 viol = fmaxf(viol, vi);
             }
@@ -1073,18 +1088,22 @@ __device__ float cta_certificate(const CCtx<D>& c) {
     }
     if constexpr (BOX) {
         // state boxes: violation max(x - hi, lo - x, 0) / (kc + |bound|), and
-        // |nu (x - b)| of the active bounds whose multiplier counts
+        // |nu (x - b)| of the active bounds whose multiplier counts; both
+        // weighted by kBoxFeasWeight unless the scan held the bound exactly
+        // (it then sits on its bound to rounding)
         for (int e = tid; e < c.Nh * NX; e += kPT) {
             const int k = e / NX, i = e % NX;
             const float lo = c.box[(k * 2) * NX + i], hi = c.box[(k * 2 + 1) * NX + i];
             const float x = c.xr()[(k + 1) * NX + i];
-            if (x > hi) feas = fmaxf(feas, (x - hi) / (c.kc + fabsf(hi)));
-            if (x < lo) feas = fmaxf(feas, (lo - x) / (c.kc + fabsf(lo)));
             float bnd;
             bool up;
-            if (c.box_active(k, i, &bnd, &up)) {
+            const bool act = c.box_active(k, i, &bnd, &up);
+            const float wgt = ((c.dbits()[k] >> i) & 1u) ? 1.0f : kBoxFeasWeight;
+            if (x > hi) feas = fmaxf(feas, wgt * (x - hi) / (c.kc + fabsf(hi)));
+            if (x < lo) feas = fmaxf(feas, wgt * (lo - x) / (c.kc + fabsf(lo)));
+            if (act) {
                 const float v = c.nub()[e];
-                if (up ? v >= 0.0f : v <= 0.0f) comp = fmaxf(comp, fabsf(v * (x - bnd)));
+                if (up ? v >= 0.0f : v <= 0.0f) comp = fmaxf(comp, wgt * fabsf(v * (x - bnd)));
             }
         }
     }
@@ -1139,6 +1158,7 @@ __device__ bool cta_refine_modes(const CCtx<D>& c, float alpha) {
                     c.nub()[e] = 0.0f;
                     c.rhob()[e] = kBoxPenalty;
                     c.dprev()[e] = INFINITY;
+                    c.dlast()[e] = 0.0f;
                 }
                 if (clr) atomicAnd(c.sbits() + k, ~clr);
             }

@@ -20,13 +20,18 @@ input of its own stage acts.  A bound the inputs reach only through a
 velocity (the CoM height) is held by an augmented Lagrangian whose multiplier converges at rate
 h / (h + penalty), h the cost of moving the component (up to 3e6 for the CoM
 height); its penalty grows until the bound holds, capped at 1e7 where FP32
-Riccati sums lose the other terms, so CoM-height boxes mostly stop at the
+Riccati sums lose the other terms, and while the penalty stays the
+multiplier step extrapolates the geometric sequence to its limit.  Such a
+bound is stiff: the certificate weights its violation and complementarity
+10x, so that a certified point holds it closely enough for the u and
+objective bars.  CoM-height boxes that still miss the tolerance stop at the
 iteration cap, or stall on their faces, and say so (MPC_MAX_ITER or
 MPC_STALLED, certificate above the tolerance).
 Measured over 20 seeds of these batches (B300): vertical-velocity boxes
 320/320 (walking) and 220/220 (foot wrenches) certified, forward-velocity
-boxes 320/320 and 200/200, CoM-height boxes 30/320 and 5/220.  Every
-certified instance must match the oracle."""
+boxes 320/320 and 200/200, CoM-height boxes 100/320 and 35/220 (30/320 and
+5/220 without the extrapolation).  Every certified instance must match the
+oracle; the comparison takes certified CoM-height instances too."""
 import numpy as np
 import pytest
 import torch
@@ -118,6 +123,8 @@ def test_state_boxes_match_the_oracle(maker, B, N):
     assert by_type[0] >= 0.9 * n_type[0], by_type  # vertical velocity, held exactly: 100 % over 20 seeds
     assert by_type[2] >= 0.9 * n_type[2], by_type  # forward velocity, held exactly: 100 %
     ids = [b for b in range(B) if ok[b]][::max(1, int(ok.sum()) // 12)]
+    ids = sorted(set(ids) | {b for b in range(1, B, 3) if ok[b]}.intersection(
+        [b for b in range(1, B, 3) if ok[b]][:4]))  # certified CoM-height instances too
     worst, n_bind = check(batch, out, ids, xlo, xhi)
     assert n_bind >= len(ids) // 2  # the boxes bind at the optimum
     print(f"{maker.__name__} N={N}: certified by bound type {by_type} of {n_type}, worst {worst:.2e}, "
