@@ -122,6 +122,10 @@ def test_state_boxes_match_the_oracle(maker, B, N):
     n_type = [len(ok[t::3]) for t in range(3)]
     assert by_type[0] >= 0.9 * n_type[0], by_type  # vertical velocity, held exactly: 100 % over 20 seeds
     assert by_type[2] >= 0.9 * n_type[2], by_type  # forward velocity, held exactly: 100 %
+    if N <= 12:
+        # CoM height, by the augmented Lagrangian: 16-31 % over 20 seeds
+        # (6 of 16 and 3 of 11 on these batches)
+        assert by_type[1] >= 0.15 * n_type[1], by_type
     ids = [b for b in range(B) if ok[b]][::max(1, int(ok.sum()) // 12)]
     ids = sorted(set(ids) | {b for b in range(1, B, 3) if ok[b]}.intersection(
         [b for b in range(1, B, 3) if ok[b]][:4]))  # certified CoM-height instances too
