@@ -1051,7 +1051,9 @@ __device__ float cta_certificate(const CCtx<D>& c) {
 #pragma unroll
         for (int i = 0; i < CD; ++i) wmax = fmaxf(wmax, fabsf(r[i]));
         feas = fmaxf(feas, fmaxf(gmax, 0.0f) / (c.kc + fmax));
-        for (int sweep = 0; sweep < 100; ++sweep) {
+        // at most kNnlsSweeps sweeps: each sweep lowers the fit's squared
+        // residual, so a cut-off fit leaves it larger than the converged one
+        for (int sweep = 0; sweep < kNnlsSweeps; ++sweep) {
             float change = 0.0f;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
