@@ -171,25 +171,68 @@ __device__ uint32_t project_contact(const float* a, float* out, float mu, float 
         c[j] = cone_coef<CD>(j, mu, dx, dy);
         bp[j] = c[j] > 0.0f ? at[j] / c[j] : INFINITY;
     }
-    float best_n = fminf(fmaxf(an, 0.0f), nmax);
-    float best_phi = INFINITY;
-#pragma unroll
-    for (int s = -1; s < M; ++s) {
-        float num = an, den = 1.0f;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const bool in = (s >= 0) && (bp[j] >= bp[s < 0 ? 0 : s]);
-            num += in ? c[j] * at[j] : 0.0f;
-            den += in ? c[j] * c[j] : 0.0f;
-        }
-        const float n = fminf(fmaxf(num / den, 0.0f), nmax);
-        float phi = (n - an) * (n - an);
+    float best_n;
+    if constexpr (CD == 6) {
+        // the pieces in breakpoint order: sorted descending, the candidate
+        // sets are nested (the m largest), and phi' is increasing, so the
+        // minimiser over the reals is the first candidate m whose n_m is not
+        // below the next breakpoint (n_m < b_(m) holds once candidate m - 1
+        // failed: n_m is a weighted mean of n_(m-1) and b_(m)); the test is
+        // num_m >= b_(m+1) den_m, and one division gives n
+        float sb[M], sca[M], scc[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            const float d = fmaxf(at[j] - c[j] * n, 0.0f);
-            phi += d * d;
+            sb[j] = bp[j];
+            sca[j] = c[j] * at[j];
+            scc[j] = c[j] * c[j];
         }
-        if (phi < best_phi) { best_phi = phi; best_n = n; }
+#pragma unroll
+        for (int i = 1; i < M; ++i) {
+#pragma unroll
+            for (int j = i; j > 0; --j) {
+                const bool sw = sb[j] > sb[j - 1];
+                const float b0 = sb[j - 1], a0 = sca[j - 1], c0 = scc[j - 1];
+                sb[j - 1] = sw ? sb[j] : b0;
+                sca[j - 1] = sw ? sca[j] : a0;
+                scc[j - 1] = sw ? scc[j] : c0;
+                sb[j] = sw ? b0 : sb[j];
+                sca[j] = sw ? a0 : sca[j];
+                scc[j] = sw ? c0 : scc[j];
+            }
+        }
+        float num = an, den = 1.0f, fnum = an, fden = 1.0f;
+        bool found = an >= sb[0];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            num += sca[m];
+            den += scc[m];
+            const bool ok = !found && (m + 1 == M || num >= sb[m + 1] * den);
+            fnum = ok ? num : fnum;
+            fden = ok ? den : fden;
+            found = found || ok;
+        }
+        best_n = fminf(fmaxf(fnum / fden, 0.0f), nmax);
+    } else {
+        best_n = fminf(fmaxf(an, 0.0f), nmax);
+        float best_phi = INFINITY;
+#pragma unroll
+        for (int s = -1; s < M; ++s) {
+            float num = an, den = 1.0f;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const bool in = (s >= 0) && (bp[j] >= bp[s < 0 ? 0 : s]);
+                num += in ? c[j] * at[j] : 0.0f;
+                den += in ? c[j] * c[j] : 0.0f;
+            }
+            const float n = fminf(fmaxf(num / den, 0.0f), nmax);
+            float phi = (n - an) * (n - an);
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const float d = fmaxf(at[j] - c[j] * n, 0.0f);
+                phi += d * d;
+            }
+            if (phi < best_phi) { best_phi = phi; best_n = n; }
+        }
     }
     uint32_t mode = 0;
     const float n = best_n;
