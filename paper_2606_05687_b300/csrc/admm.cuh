@@ -123,17 +123,14 @@ __device__ __forceinline__ uint32_t project_point(const float* a, float* out, fl
                                                   float ir2) {
     const float ax = a[0], ay = a[1], an = a[2];
     const float tx = fabsf(ax), ty = fabsf(ay);
-    const float n0 = fminf(fmaxf(an, 0.0f), nmax);
-    const float n1 = fminf(fmaxf(fmaf(mu, fmaxf(tx, ty), an) * ir1, 0.0f), nmax);
-    const float n2 = fminf(fmaxf(fmaf(mu, tx + ty, an) * ir2, 0.0f), nmax);
-    auto phi = [&](float n) {
-        const float dn = n - an, ex = fmaxf(fmaf(-mu, n, tx), 0.0f), ey = fmaxf(fmaf(-mu, n, ty), 0.0f);
-        return fmaf(dn, dn, fmaf(ex, ex, ey * ey));
-    };
-    float n = n0, best = phi(n0);
-    const float p1 = phi(n1), p2 = phi(n2);
-    if (p1 < best) { best = p1; n = n1; }
-    if (p2 < best) n = n2;
+    // the pieces in breakpoint order (b = |t| / mu): the minimiser over the
+    // reals is the first candidate whose n is not below the next breakpoint
+    // (none clipped: n = a_n >= b_max; the larger clipped: n_1 >= b_min;
+    // else both), clamped to [0, nmax]
+    const float tmax = fmaxf(tx, ty), tmin = fminf(tx, ty);
+    const float u1 = fmaf(mu, tmax, an) * ir1, u2 = fmaf(mu, tx + ty, an) * ir2;
+    const float nu = (mu * an >= tmax) ? an : ((mu * u1 >= tmin) ? u1 : u2);
+    const float n = fminf(fmaxf(nu, 0.0f), nmax);
     uint32_t mode = 0;
     if (n <= 0.0f) mode |= 1u << 4;
     if (n >= nmax) mode |= 1u << 5;
