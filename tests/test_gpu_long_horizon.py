@@ -140,3 +140,25 @@ def test_refinement_breaks_an_active_set_cycle(pinmpc):
     assert out["status"][0] == pinmpc.CONVERGED
     assert out["iters"][0] <= 312 and out["polishes"][0] <= 32, (out["iters"][0], out["polishes"][0])
     compare(sub, out, [0])
+
+
+def test_stalled_points_meet_the_oracle_bars(pinmpc):
+    """Every instance of the 64-stage walking batch that stalls (15 of 4096,
+    each at the certificate's FP32 floor) returns a point within the oracle
+    bars: u and xi within 1e-4, the checker's KKT within 1e-5, the objective
+    within 1e-6 (measured worst: 1.3e-6, 3.7e-6, 6.8e-8)."""
+    batch = W.generate(W.rl_scale_walking(B=4096, N=64, seed=1077))
+    out = pinmpc.solve_workload(batch)
+    ids = np.flatnonzero(out["status"] == pinmpc.STALLED)
+    assert 0 < len(ids) <= 40, len(ids)
+    assert np.all((out["status"] == pinmpc.CONVERGED) | (out["status"] == pinmpc.STALLED))
+    for b in ids:
+        inst = qp.instance(batch, int(b))
+        sol = qp.solve_instance(inst)
+        u = out["u"][b].astype(np.float64)
+        xi = out["xi"][b].astype(np.float64)
+        rep = okkt.kkt_residual(inst, xi, u)
+        assert np.abs(u - sol.u).max() <= REL_TRAJ * np.abs(sol.u).max(), b
+        assert np.abs(xi - sol.xi).max() <= REL_TRAJ * np.abs(sol.xi).max(), b
+        assert rep.kkt <= KKT_TOL, (b, rep.kkt)
+        assert abs(qp.objective(inst, xi, u) - sol.objective) <= OBJ_GAP * abs(sol.objective), b
